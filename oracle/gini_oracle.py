@@ -1,0 +1,189 @@
+"""ctypes binding of the FP64 CPU oracle (gini_oracle.c).
+
+TEST INFRASTRUCTURE ONLY: tests/, __graft_entry__.smoke() and the CPU-baseline
+/ reference arm of bench.py are the only users.  The product path never imports
+this module.  Nothing here computes the method itself: every function forwards
+to the C oracle, whose header lists the paper passages each routine follows.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "gini_oracle.c")
+_OUT = os.path.join(_HERE, "_build", "liborcgini.so")
+_lib = None
+
+_F64P = ctypes.POINTER(ctypes.c_double)
+_F32P = ctypes.POINTER(ctypes.c_float)
+_I64P = ctypes.POINTER(ctypes.c_int64)
+_I32P = ctypes.POINTER(ctypes.c_int32)
+_I64 = ctypes.c_int64
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (IEEE double, no contraction, OpenMP)."""
+    if force or not os.path.exists(_OUT) or os.path.getmtime(_OUT) < os.path.getmtime(_SRC):
+        os.makedirs(os.path.dirname(_OUT), exist_ok=True)
+        tmp = _OUT + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fopenmp",
+                               "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, _OUT)
+    return _OUT
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_OUT)
+        L.orc_midrank2.argtypes = [_F64P, _I64, _I32P]
+        L.orc_gini_norm.argtypes = [_F64P, _I64]
+        L.orc_gini_norm.restype = ctypes.c_double
+        L.orc_gini_dg.argtypes = [_F64P, _F64P, _I64]
+        L.orc_gini_dg.restype = ctypes.c_double
+        L.orc_pd.argtypes = [_F64P, _F64P, _I64, ctypes.c_double]
+        L.orc_pd.restype = ctypes.c_double
+        L.orc_pd_grad.argtypes = [_F64P, _F64P, _I64, ctypes.c_double, _F64P]
+        L.orc_pd_grad.restype = ctypes.c_double
+        L.orc_delta.argtypes = [_F32P, _I64, _I64, _I64, _F64P, ctypes.c_int, _F64P, _F64P]
+        L.orc_delta_pairs.argtypes = [_F32P, _I64, _I64, _I64, _F64P, ctypes.c_int,
+                                      _I64P, _I64P, _I64, _F64P]
+        L.orc_embed_dist_pairs.argtypes = [_F64P, _I64, ctypes.c_int, ctypes.c_double,
+                                           _I64P, _I64P, _I64, _F64P]
+        L.orc_stress_grad.argtypes = [_F64P, _I64, ctypes.c_int, ctypes.c_double, _F64P,
+                                      _I64, ctypes.c_double, _F64P]
+        L.orc_stress_grad.restype = ctypes.c_double
+        L.orc_grad_rows.argtypes = [_F64P, _I64, ctypes.c_int, ctypes.c_double, _F64P,
+                                    _I64P, _I64, ctypes.c_double, _F64P]
+        L.orc_fit.argtypes = [_F64P, _I64, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                              ctypes.c_double, ctypes.c_int, _F64P, _F64P]
+        L.orc_set_threads.argtypes = [ctypes.c_int]
+        L.orc_get_threads.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _p(a, t):
+    return a.ctypes.data_as(t)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _f32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def set_threads(t: int) -> None:
+    lib().orc_set_threads(int(t))
+
+
+def get_threads() -> int:
+    return int(lib().orc_get_threads())
+
+
+def midrank2(v) -> np.ndarray:
+    """Twice the midrank of each element of one vector."""
+    v = _f64(v)
+    out = np.empty(v.shape[0], dtype=np.int32)
+    lib().orc_midrank2(_p(v, _F64P), v.shape[0], _p(out, _I32P))
+    return out
+
+
+def gini_norm(x) -> float:
+    x = _f64(x)
+    return float(lib().orc_gini_norm(_p(x, _F64P), x.shape[0]))
+
+
+def gini_dg(x, y) -> float:
+    x, y = _f64(x), _f64(y)
+    return float(lib().orc_gini_dg(_p(x, _F64P), _p(y, _F64P), x.shape[0]))
+
+
+def pd(x, y, nu: float) -> float:
+    """Symmetrized generalized Gini pseudo-distance of two vectors."""
+    x, y = _f64(x), _f64(y)
+    return float(lib().orc_pd(_p(x, _F64P), _p(y, _F64P), x.shape[0], float(nu)))
+
+
+def pd_grad(x, y, nu: float):
+    """(Dbar(x, y), dDbar/dz) with z = x - y, ranks held fixed."""
+    x, y = _f64(x), _f64(y)
+    dz = np.empty(x.shape[0], dtype=np.float64)
+    v = lib().orc_pd_grad(_p(x, _F64P), _p(y, _F64P), x.shape[0], float(nu), _p(dz, _F64P))
+    return float(v), dz
+
+
+def delta(X, nus):
+    """Full Delta (len(nus), n, n) and sum_{i<j} delta^2 per nu."""
+    X = _f32(X)
+    nus = _f64(np.atleast_1d(nus))
+    n, p = X.shape
+    D = np.empty((nus.shape[0], n, n), dtype=np.float64)
+    s = np.empty(nus.shape[0], dtype=np.float64)
+    lib().orc_delta(_p(X, _F32P), n, p, p, _p(nus, _F64P), nus.shape[0], _p(D, _F64P),
+                    _p(s, _F64P))
+    return D, s
+
+
+def delta_pairs(X, nus, I, J) -> np.ndarray:
+    """delta for listed pairs, shape (npairs, len(nus))."""
+    X = _f32(X)
+    nus = _f64(np.atleast_1d(nus))
+    I = np.ascontiguousarray(I, dtype=np.int64)
+    J = np.ascontiguousarray(J, dtype=np.int64)
+    n, p = X.shape
+    out = np.empty((I.shape[0], nus.shape[0]), dtype=np.float64)
+    lib().orc_delta_pairs(_p(X, _F32P), n, p, p, _p(nus, _F64P), nus.shape[0],
+                          _p(I, _I64P), _p(J, _I64P), I.shape[0], _p(out, _F64P))
+    return out
+
+
+def embed_dist_pairs(Y, nu, I, J) -> np.ndarray:
+    Y = _f64(Y)
+    I = np.ascontiguousarray(I, dtype=np.int64)
+    J = np.ascontiguousarray(J, dtype=np.int64)
+    out = np.empty(I.shape[0], dtype=np.float64)
+    lib().orc_embed_dist_pairs(_p(Y, _F64P), Y.shape[0], Y.shape[1], float(nu),
+                               _p(I, _I64P), _p(J, _I64P), I.shape[0], _p(out, _F64P))
+    return out
+
+
+def stress_grad(Y, nu, Delta, sum_delta2, grad: bool = True):
+    """(S, dS/dY or None) with S = sum_{i<j} r_ij^2 / sum_delta2."""
+    Y = _f64(Y)
+    Delta = _f64(Delta)
+    n, k = Y.shape
+    g = np.empty((n, k), dtype=np.float64) if grad else None
+    S = lib().orc_stress_grad(_p(Y, _F64P), n, k, float(nu), _p(Delta, _F64P),
+                              Delta.shape[1], float(sum_delta2),
+                              _p(g, _F64P) if grad else None)
+    return float(S), g
+
+
+def grad_rows(Y, nu, Delta_rows, rows, sum_delta2) -> np.ndarray:
+    Y = _f64(Y)
+    Delta_rows = _f64(Delta_rows)
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    n, k = Y.shape
+    g = np.empty((rows.shape[0], k), dtype=np.float64)
+    lib().orc_grad_rows(_p(Y, _F64P), n, k, float(nu), _p(Delta_rows, _F64P),
+                        _p(rows, _I64P), rows.shape[0], float(sum_delta2), _p(g, _F64P))
+    return g
+
+
+def fit(Delta, nu, sum_delta2, Y0, eta, T):
+    """T fixed-step GD iterations; returns (Y_T, history[T+1])."""
+    Delta = _f64(Delta)
+    Y = _f64(Y0).copy()
+    n, k = Y.shape
+    h = np.empty(T + 1, dtype=np.float64)
+    lib().orc_fit(_p(Delta, _F64P), n, k, float(nu), float(sum_delta2), float(eta), int(T),
+                  _p(Y, _F64P), _p(h, _F64P))
+    return Y, h
