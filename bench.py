@@ -1,0 +1,424 @@
+"""Benchmark of the Gini-MDS hot path on GB300.
+
+One step = one whole Gini-MDS fit of the image-like workload (n = 20,000
+points, p = 784, k = 2, nu = 2, T = 200): the Delta build (sort of every pair's
+difference vector, midrank weights, BF16 hi+lo tiled store, FP64 sum of
+squares) followed by 200 fused stress+adjoint iterations (BF16 hi plane, the
+last 40 reading hi+lo) and the final FP64 stress.  Inputs are resident in HBM
+when the timed region starts; L2 is flushed between steps.
+
+  value   = iterations per second of whole fits (T * steps / time of the steps,
+            each step including its Delta build)
+  e2e     = the same through the public host API (host X and Y0 copied in,
+            Y_T and S(Y_T) copied out, inside the timed region)
+
+Also reported: the Delta build on its own (useful TFLOP/s, ranked elements/s),
+the iteration phase on its own, and the plain FP32 form (full square FP32
+Delta, separate forward and adjoint kernels) at the same configuration.
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload and extrapolates (there is no reference implementation to run).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gini-MDS iters/s at n=20k,k=2 and Δ-build TFLOP/s, chosen vs plain FP32 form"
+WORKLOAD = "image-n20000-p784"
+POLISH = 40
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain-form comparison")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    return ap.parse_args()
+
+
+def _dist_init(args):
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend)
+    return rank, local, world
+
+
+def _barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def _max_over_ranks(v, world):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64,
+                     device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.gpu = gpu_index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.p = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+
+    def summary(self):
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        load = [s for s in sm if mx and s >= 0.5 * max(mx)] or sm
+        return {"sm_mhz": statistics.median(load) if load else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+def _profile_traffic():
+    """DRAM bytes per launch of the Delta-build kernel from the committed ncu
+    summary (scaled to this workload), or None."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f)
+    return {}
+
+
+def run_ours(args, rank, local, world):
+    import numpy as np
+    import torch
+
+    import paper_2605_25124_gb300 as G
+    from paper_2605_25124_gb300 import _lib
+    from paper_2605_25124_gb300 import build as gb
+    from paper_2605_25124_gb300 import workloads as wl
+
+    gb.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = wl.WORKLOADS[args.workload]
+    n, p, k, T = w["n"], w["p"], w["k"], w["iters"]
+    nu = float(w["nu"][0])
+    X_host = wl.make_X(args.workload)
+    Y0_host = wl.y_init(n, k, seed=w["seed"] + 1000)
+    X = torch.from_numpy(X_host).to(dev)
+    Y0 = torch.from_numpy(Y0_host).to(dev)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    ws = G.workspace(dev)
+    Yout = torch.empty_like(Y0)
+
+    def step(ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        mats, _ = G.gini_dist(X, [nu], layout="tiled", dtype="bf16x2", ws=ws,
+                              check_errors=False)
+        if ev is not None:
+            ev[1].record(stream)
+        D = mats[0]
+        eta = G.default_step(n, k, nu, D.sum_delta2, 1.0)
+        Y, _, final = G.gini_mds_fit(Y0, nu, D, eta, T, polish_iters=POLISH, history=False,
+                                     ws=ws, check_errors=False, out=Yout)
+        if ev is not None:
+            ev[2].record(stream)
+        return final, D
+
+    for _ in range(args.warmup):
+        step()
+    ws.check()
+    torch.cuda.synchronize()
+
+    L = _lib.lib()
+    launches0 = L.gini_launch_count()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    finals = []
+    with ClockSampler(local) as clk:
+        for s in range(args.steps):
+            flush.zero_()  # evict L2 between steps (outside the timed events)
+            _barrier(world)
+            torch.cuda.synchronize()
+            f, D = step(evs[s])
+            finals.append(f)
+            torch.cuda.synchronize()
+            _barrier(world)
+    launches = L.gini_launch_count() - launches0
+    ws.check()
+    build_ms = [e[0].elapsed_time(e[1]) for e in evs]
+    iter_ms = [e[1].elapsed_time(e[2]) for e in evs]
+    step_ms = [a + b for a, b in zip(build_ms, iter_ms)]
+    total_s = _max_over_ranks(sum(step_ms) / 1e3, world)
+    value = world * T * args.steps / total_s
+    final_stress = float(finals[-1])
+    clocks = clk.summary()
+
+    # Delta build: useful work = P pairs x (p subtractions + p multiply-adds
+    # per nu) = 3 p flops per pair and nu; ranked elements = P p.
+    P = n * (n - 1) // 2
+    b_s = statistics.mean(build_ms) / 1e3
+    build_tflops = 3.0 * p * P / b_s / 1e12
+    ranked_per_s = P * p / b_s
+    # ALU roofline of the sort: comparison lower bound p ceil(log2 p) per pair
+    # plus the 3p useful flops, against one op per FP32 lane per clock.
+    ops_per_pair = p * math.ceil(math.log2(p)) + 3 * p
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    max_mhz = clocks.get("sm_max_mhz") or 2070.0
+    alu_peak = sms * 128 * max_mhz * 1e6
+    achieved_ops = P * ops_per_pair / b_s
+    traffic = _profile_traffic()
+
+    # iteration phase: BF16 hi plane 2 bytes per stored element (hi+lo = 4 in the
+    # polish iterations); algorithmic bytes = P pairs x bytes per pair.
+    it_s = statistics.mean(iter_ms) / 1e3 / (T + 1)
+    plane = G.tiled_elems(n)
+    bytes_iter = P * (2 * (T - POLISH) + 4 * POLISH) / T
+    hbm_peak, peak_src = _peaks()
+    iter_gbs = bytes_iter / it_s / 1e9
+
+    out = {
+        "metric": METRIC, "value": round(value, 3), "unit": "iters/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(statistics.mean(step_ms), 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded image-like 28x28 blobs + noise, clipped; MNIST not available)",
+        "config": {"workload": args.workload, "n": n, "p": p, "k": k, "nu": nu, "iters": T,
+                   "delta_storage": "tiled bf16 hi+lo (hi plane for the first "
+                                    f"{T - POLISH} iterations)",
+                   "l2": "flushed between steps (256 MB write)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "roofline": {"kernel": "k_dist (Delta build: pair sort + midrank weights)",
+                     "bound": "alu", "achieved": round(achieved_ops / 1e12, 3),
+                     "peak": round(alu_peak / 1e12, 3), "unit": "Tops/s",
+                     "frac": round(achieved_ops / alu_peak, 4),
+                     "traffic": traffic.get("k_dist_bytes_per_launch"),
+                     "peak_note": f"{sms} SMs x 128 FP32 lanes x {max_mhz:.0f} MHz",
+                     "work_note": "per pair p*ceil(log2 p) compares + 3p flops"},
+        "iter_roofline": {"kernel": "k_fused2 (+ k_update) per iteration", "bound": "hbm",
+                          "achieved": round(iter_gbs, 1), "peak": hbm_peak, "unit": "GB/s",
+                          "frac": round(iter_gbs / hbm_peak, 4), "peak_source": peak_src,
+                          "traffic": traffic.get("k_fused2_bytes_per_launch")},
+        "phases": {"delta_build_ms": round(statistics.mean(build_ms), 3),
+                   "delta_build_tflops": round(build_tflops, 4),
+                   "ranked_elements_per_s": float(f"{ranked_per_s:.4e}"),
+                   "iter_ms": round(it_s * 1e3, 5),
+                   "iters_per_s_iteration_phase": round(1.0 / it_s, 1),
+                   "final_stress": final_stress},
+        "clocks": clocks,
+        "gpu_launches": int(launches),
+    }
+
+    if not args.no_plain and rank == 0:
+        out["plain_fp32"] = _plain(G, X, Y0, n, k, nu, T, stream, final_stress)
+    out["e2e"] = _e2e(G, X_host, Y0_host, n, p, k, nu, T, args, world)
+    if rank == 0 and not args.no_cpu:
+        out["cpu_baseline"] = cpu_baseline(args.workload, budget_s=12.0)
+    return out
+
+
+def _plain(G, X, Y0, n, k, nu, T, stream, chosen_final):
+    import torch
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    mats, _ = G.gini_dist(X, [nu], layout="full", dtype="f32", check_errors=False)
+    ev[1].record(stream)
+    D = mats[0]
+    eta = G.default_step(n, k, nu, D.sum_delta2, 1.0)
+    _, _, final = G.gini_mds_fit(Y0, nu, D, eta, T, history=False, check_errors=False)
+    ev[2].record(stream)
+    torch.cuda.synchronize()
+    b = ev[0].elapsed_time(ev[1])
+    it = ev[1].elapsed_time(ev[2]) / (T + 1)
+    f = float(final)
+    del mats, D
+    torch.cuda.empty_cache()
+    return {"form": "full-square FP32 Delta, separate forward and adjoint kernels",
+            "delta_build_ms": round(b, 3), "iter_ms": round(it, 5),
+            "iters_per_s_iteration_phase": round(1e3 / it, 1),
+            "iters_per_s_whole_fit": round(T / ((b + it * (T + 1)) / 1e3), 3),
+            "final_stress": f,
+            "chosen_vs_plain_final_stress_rel_diff": abs(chosen_final - f) / f}
+
+
+def _e2e(G, X_host, Y0_host, n, p, k, nu, T, args, world):
+    import torch
+    ts = []
+    for i in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        _barrier(world)
+        t0 = time.perf_counter()
+        Y, fin, _ = G.fit_host(X_host, nu, k, T, Y0_host, dtype="bf16x2", polish_iters=POLISH)
+        t1 = time.perf_counter()
+        if i >= args.warmup:
+            ts.append(t1 - t0)
+    tot = _max_over_ranks(sum(ts), world)
+    return {"value": round(world * T * args.steps / tot, 3), "unit": "iters/s",
+            "h2d_bytes_per_step": int(X_host.nbytes + Y0_host.nbytes),
+            "d2h_bytes_per_step": int(Y0_host.nbytes + 8)}
+
+
+def cpu_baseline(workload, budget_s=12.0):
+    """The FP64 oracle as it stands, on a bounded sample of the workload,
+    extrapolated to whole-fit iterations per second."""
+    import numpy as np
+
+    from oracle import gini_oracle as orc
+    from paper_2605_25124_gb300 import workloads as wl
+
+    orc.build()
+    w = wl.WORKLOADS[workload]
+    n, p, k, T = w["n"], w["p"], w["k"], w["iters"]
+    nu = float(w["nu"][0])
+    X = wl.make_X(workload)
+    Y0 = wl.y_init(n, k, seed=w["seed"] + 1000).astype(np.float64)
+    rng = np.random.default_rng(0)
+    P = n * (n - 1) // 2
+    # Delta sample: grow until ~budget/2 seconds
+    npairs, t_pairs = 64, 0.0
+    while True:
+        I = rng.integers(0, n, npairs)
+        J = (I + 1 + rng.integers(0, n - 1, npairs)) % n
+        t0 = time.perf_counter()
+        orc.delta_pairs(X, [nu], I, J)
+        t_pairs = time.perf_counter() - t0
+        if t_pairs > budget_s / 4 or npairs >= 1 << 20:
+            break
+        npairs *= 4
+    per_pair = t_pairs / npairs
+    # iteration sample: gradient rows against all n points
+    nrows, t_rows = 4, 0.0
+    Drows = np.abs(rng.standard_normal((4096, n)))
+    while True:
+        rows = rng.choice(n, nrows, replace=False)
+        t0 = time.perf_counter()
+        orc.grad_rows(Y0, nu, Drows[:nrows], rows, 1.0)
+        t_rows = time.perf_counter() - t0
+        if t_rows > budget_s / 4 or nrows >= 4096:
+            break
+        nrows *= 4
+    per_row = t_rows / nrows
+    t_delta = per_pair * P
+    t_iter = per_row * n
+    value = T / (t_delta + (T + 1) * t_iter)
+    return {"value": float(f"{value:.4e}"), "unit": "iters/s", "cores": orc.get_threads(),
+            "kind": "oracle",
+            "sample": (f"Delta: {npairs} random pairs of {P} (p={p}, nu={nu}), "
+                       f"{per_pair * 1e3:.3f} ms/pair; iteration: gradient rows {nrows} of {n}, "
+                       f"{per_row * 1e3:.3f} ms/row; extrapolated to Delta build + {T + 1} "
+                       "stress/gradient passes"),
+            "extrapolated_fit_s": round(t_delta + (T + 1) * t_iter, 1)}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    t0 = time.perf_counter()
+    cb = None
+    vals = []
+    for i in range(args.warmup + args.steps):
+        c = cpu_baseline(args.workload, budget_s=max(2.0, 40.0 / (args.warmup + args.steps)))
+        if i >= args.warmup:
+            vals.append(c["value"])
+            cb = c
+    v = statistics.mean(vals)
+    return {"metric": METRIC, "value": float(f"{v:.4e}"), "unit": "iters/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round((time.perf_counter() - t0) * 1e3 / (args.warmup + args.steps), 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded image-like 28x28 blobs + noise, clipped)",
+            "config": {"workload": args.workload, "parallelism": "host cores (OpenMP)"},
+            "impl": "reference",
+            "cpu_baseline": {"value": cb["value"], "unit": "iters/s", "cores": cb["cores"],
+                             "kind": "oracle", "sample": cb["sample"]},
+            "e2e": {"value": float(f"{v:.4e}"), "unit": "iters/s",
+                    "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = _args()
+    rank, local, world = _dist_init(args)
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+    else:
+        out = run_ours(args, rank, local, world)
+    if rank == 0 and out is not None:
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,211 @@
+/*
+ * gini_mds.h -- C ABI of libginimds.so, the sm_103a (GB300) Gini-MDS library.
+ *
+ * What it computes (Mussard & Mussard, "Optimizing Multidimensional Scaling in
+ * Gini Metric Spaces"):
+ *   - midranks of the components of a vector (Definition 1, Eq. (rank-ties));
+ *   - the symmetrized generalized Gini pseudo-distance of Section III-B,
+ *       Dbar_{G,nu}(x,y) = 1/2 D_{G,nu}(x,y) + 1/2 D_{G,nu}(y,x),
+ *       D_{G,nu}(x,y)    = -d sum_j z_j (Fbar^{nu-1}(z_j) - Fbar^{nu-1}(0)),
+ *     z = x - y, ranks taken across the d components of z, midranks for ties,
+ *     Fbar(t) = 1 - R(t)/d.  The two terms combine into
+ *       Dbar = (d/2) sum_j z_j W(R_j),  W(R) = ((R-1)/d)^{nu-1} - ((d-R)/d)^{nu-1},
+ *     which is what the kernels evaluate;
+ *   - the dissimilarity matrix Delta = [Dbar(x_i, x_j)] (Algorithm 1);
+ *   - Kruskal's stress (Section IV-B) between Delta and the pseudo-distances of
+ *     an embedding Y (n x k), normalized as S = sum_{i<j} (d_ij - delta_ij)^2 /
+ *     sum_{i<j} delta_ij^2 (KS = sqrt(S)), and its gradient with the ranks held
+ *     fixed;
+ *   - fixed-step gradient descent on S ("Run MDS" of Algorithm 1).
+ *
+ * Conventions for every entry point:
+ *   - Pointers named *_dev are device memory owned by the caller; pointers
+ *     named *_host are host memory owned by the caller.  The library never
+ *     allocates device memory: scratch space comes from the caller's
+ *     workspace `ws` of `ws_bytes` bytes (see gini_workspace_size).  A fresh
+ *     workspace must be zero-filled once before first use.
+ *   - Work is enqueued on `stream` (a cudaStream_t passed as void*; NULL is
+ *     the legacy default stream) and runs asynchronously.  Argument errors are
+ *     detected on the host and returned immediately, before anything is
+ *     enqueued.  Errors found by the kernels (non-finite data, an expired
+ *     bounded wait) are recorded in the workspace and returned by gini_check.
+ *   - Return values are gini_status codes.
+ *   - Row-major storage; leading dimensions are in elements.
+ */
+#ifndef GINI_MDS_H
+#define GINI_MDS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  GINI_OK = 0,
+  GINI_EINVAL = 1,      /* invalid argument: size, null pointer, alignment, nu <= 1 */
+  GINI_ENONFINITE = 2,  /* NaN or Inf in the input (reported by gini_check) */
+  GINI_EDEGENERATE = 3, /* sum of squared dissimilarities is zero: stress undefined */
+  GINI_ENOMEM = 4,      /* workspace smaller than gini_workspace_size */
+  GINI_ECUDA = 5,       /* a CUDA runtime call failed (see gini_last_cuda_error) */
+  GINI_ETIMEOUT = 6     /* a bounded device-side wait expired (reported by gini_check) */
+} gini_status;
+
+/* Storage type of a dissimilarity matrix. */
+typedef enum {
+  GINI_F32 = 0,     /* float */
+  GINI_BF16 = 1,    /* bfloat16, round to nearest */
+  GINI_BF16X2 = 2,  /* two bfloat16 planes, hi = bf16(delta), lo = bf16(delta - hi) */
+  GINI_FP8E4M3 = 3  /* e4m3 with a float scale per column: delta ~ q * col_scale[j] */
+} gini_dtype;
+
+/* Layout of a dissimilarity matrix. */
+typedef enum {
+  /* n x n, leading dimension ldd, symmetric, zero diagonal.  F32 only. */
+  GINI_LAYOUT_FULL = 0,
+  /* Upper triangle in B x B tiles (B = gini_tile_size()).  Tiles (I, J) with
+   * I <= J are stored one after another in row-major order of (I, J); inside
+   * a tile, element (r, c) is at r*B + c and holds delta(I*B + r, J*B + c).
+   * Only entries with row < column and both < n are meaningful; the rest are
+   * never read.  One plane holds gini_tiled_elems(n) elements; GINI_BF16X2
+   * stores the lo plane right after the hi plane. */
+  GINI_LAYOUT_TILED = 1
+} gini_layout;
+
+/* Workspace queries (see gini_workspace_size). */
+typedef enum {
+  GINI_OP_RANK = 0,
+  GINI_OP_DIST = 1,
+  GINI_OP_STRESS = 2,
+  GINI_OP_FIT = 3
+} gini_op;
+
+/* Human-readable name of a status code (static string). */
+const char* gini_status_str(int status);
+
+/* Last CUDA error string recorded by a failing call on this thread. */
+const char* gini_last_cuda_error(void);
+
+/* ABI version of this header (incremented on incompatible change). */
+int gini_version(void);
+
+/* Number of kernels the library has launched in this process (all threads,
+ * all devices), for launch accounting by callers. */
+uint64_t gini_launch_count(void);
+
+/* Tile edge B of GINI_LAYOUT_TILED. */
+int gini_tile_size(void);
+
+/* Elements in one plane of the tiled upper triangle for n points:
+ * T(T+1)/2 * B*B with T = ceil(n / B). */
+int64_t gini_tiled_elems(int64_t n);
+
+/* Bytes of workspace that `op` needs.  n: points (or segments for RANK);
+ * m: vector length (features p for DIST, segment length for RANK); k:
+ * embedding dimension; iters: iterations (FIT).  Unused arguments are ignored.
+ * Returns 0 for an unknown op. */
+size_t gini_workspace_size(int op, int64_t n, int64_t m, int k, int iters);
+
+/* Synchronizes `stream`, then returns and clears the status the kernels
+ * recorded in `ws` since the last gini_check (GINI_OK, GINI_ENONFINITE or
+ * GINI_ETIMEOUT), or GINI_ECUDA if the stream reports an error. */
+int gini_check(void* ws, void* stream);
+
+/* Segmented midranks (Definition 1 with midpoint ranks for ties,
+ * Eq. (rank-ties)).
+ *   v_dev     [nseg][ld] float, segment s = v_dev[s*ld .. s*ld + m)
+ *   rank2_dev [nseg][m] int32 out: rank2[s*m + a] = 2 R(v_a)
+ *             = 2 #{b: v_b < v_a} + #{b: v_b == v_a} + 1  (exact integers;
+ *             -0.0 and +0.0 are equal)
+ * 1 <= m <= 1024, ld >= m.  NaN/Inf inputs are reported as GINI_ENONFINITE
+ * by gini_check (their ranks are then unspecified). */
+int gini_rank(const float* v_dev, int64_t nseg, int64_t m, int64_t ld, int32_t* rank2_dev,
+              void* ws, size_t ws_bytes, void* stream);
+
+/* Dissimilarity matrices Delta_q = [Dbar_{G,nu_q}(x_i, x_j)] for every nu_q
+ * (Section III-B; Algorithm 1, "Compute Gini pseudo-distances"), one sort of
+ * each pair's difference vector serving all nu values.
+ *   X_dev      [n][ldx] float data, 2 <= n, 1 <= p <= 1024, ldx >= p
+ *   nu_host    n_nu values, each > 1 and finite, 1 <= n_nu <= 8
+ *   layout, dtype: GINI_LAYOUT_FULL with GINI_F32, or GINI_LAYOUT_TILED with
+ *              GINI_F32, GINI_BF16 or GINI_BF16X2 (FP8 goes through gini_pack)
+ *   delta_dev  output; matrix q starts at element q * nu_stride (in elements
+ *              of the storage type; for BF16X2 the stride covers both planes)
+ *   ldd        leading dimension of a FULL matrix (>= n); ignored for TILED
+ *   sum_delta2_dev  n_nu doubles out: sum_{i<j} delta_ij^2 (FP32 values,
+ *              FP64 sum), or NULL
+ * The differences x_i - x_j are formed in FP32 and ranked exactly as FP32
+ * values.  Non-finite X is reported as GINI_ENONFINITE by gini_check. */
+int gini_dist(const float* X_dev, int64_t n, int64_t p, int64_t ldx, const double* nu_host,
+              int n_nu, int layout, int dtype, void* delta_dev, int64_t ldd, int64_t nu_stride,
+              double* sum_delta2_dev, void* ws, size_t ws_bytes, void* stream);
+
+/* Converts a FULL F32 dissimilarity matrix (n x n, leading dimension ldd) to
+ * the TILED layout of `dtype`.  For GINI_FP8E4M3, col_scale_dev (n floats,
+ * out) receives max_{i<j} |delta_ij| / 448 for column j (1 if the column is
+ * all zero) and the tile holds e4m3(delta_ij / col_scale[j]) (saturating);
+ * col_scale_dev is ignored otherwise.  packed_dev needs gini_tiled_elems(n)
+ * elements (two planes for BF16X2). */
+int gini_pack(const float* delta_full_dev, int64_t n, int64_t ldd, int dtype, void* packed_dev,
+              float* col_scale_dev, void* stream);
+
+/* Normalized Kruskal stress and its gradient for an embedding
+ * (Section IV-B; the embedding distance is Dbar_{G,nu} in k dimensions):
+ *   S = sum_{i<j} (d_ij - delta_ij)^2 / sum_delta2,  d_ij = Dbar_{G,nu}(y_i, y_j)
+ *   dS/dy_i = sum_{j != i} 2 (d_ij - delta_ij) / sum_delta2 * dd_ij/dy_i
+ * with the ranks of y_i - y_j held fixed (subgradient W(midrank) at ties).
+ *   Y_dev       [n][k] float, 2 <= n, 2 <= k <= 8 (k = 1 makes every
+ *               pseudo-distance zero and is rejected)
+ *   delta_dev   dissimilarities in (layout, dtype); FULL requires F32.
+ *               BF16X2 reads both planes.  col_scale_dev for FP8, else NULL.
+ *   ldd         leading dimension for FULL, ignored for TILED
+ *   sum_delta2  > 0 (GINI_EDEGENERATE otherwise)
+ *   stress_dev  1 double out: S (FP64 reduction)
+ *   grad_dev    [n][k] float out, or NULL for the stress only
+ * FULL runs the plain form: a forward kernel over i<j, then an adjoint kernel
+ * that recomputes every pair.  TILED runs the fused kernel: one pass over the
+ * stored triangle produces the stress and both row and column gradient terms. */
+int gini_stress_grad(const float* Y_dev, int64_t n, int k, double nu, const void* delta_dev,
+                     int layout, int dtype, int64_t ldd, const float* col_scale_dev,
+                     double sum_delta2, double* stress_dev, float* grad_dev, void* ws,
+                     size_t ws_bytes, void* stream);
+
+/* Arguments of gini_mds_fit. */
+typedef struct {
+  int64_t n;                  /* points, >= 2 */
+  int k;                      /* embedding dimension, 2..8 */
+  double nu;                  /* > 1 */
+  const void* delta_dev;      /* dissimilarities (layout, dtype) as in gini_stress_grad */
+  int layout;
+  int dtype;
+  int64_t ldd;
+  const float* col_scale_dev; /* FP8 only */
+  double sum_delta2;          /* > 0 */
+  double eta;                 /* fixed step on S, > 0 (see gini_default_step) */
+  int iters;                  /* T >= 0 */
+  int polish_iters;           /* BF16X2 only: the last polish_iters iterations read
+                                 hi + lo, earlier ones the hi plane only; the final
+                                 stress always reads hi + lo.  Ignored otherwise. */
+  float* Y_dev;               /* [n][k] in: Y_0, out: Y_T */
+  double* history_dev;        /* iters + 1 doubles out, S(Y_t) for t = 0..T, or NULL */
+  double* final_stress_dev;   /* 1 double out, S(Y_T), or NULL */
+} gini_fit_args;
+
+/* T iterations of Y_{t+1} = Y_t - eta * dS/dY(Y_t) (the "Run MDS" step of
+ * Algorithm 1 read as fixed-step gradient descent on Kruskal stress), then
+ * S(Y_T).  Each iteration is one pass over Delta: the TILED layout uses the
+ * fused stress+adjoint kernel, FULL the plain forward + adjoint kernels. */
+int gini_mds_fit(const gini_fit_args* args, void* ws, size_t ws_bytes, void* stream);
+
+/* A step size for gini_mds_fit: eta0 times the inverse of a Gershgorin bound
+ * on the Gauss-Newton curvature of S,
+ *   eta = eta0 * sum_delta2 / (2 (n-1) k ((k/2) w_max)^2),  w_max = ((k-1)/k)^{nu-1}.
+ * The paper gives no step rule; this one is the library's choice.  Host only. */
+double gini_default_step(int64_t n, int k, double nu, double sum_delta2, double eta0);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GINI_MDS_H */

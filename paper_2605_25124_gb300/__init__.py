@@ -1,0 +1,13 @@
+"""GB300-native (sm_103a) Gini multidimensional scaling.
+
+The compute path is libginimds.so (hand-written CUDA kernels behind a C ABI,
+include/gini_mds.h); this package is its thin Python binding.  `workloads`
+holds the seeded synthetic input generators.
+"""
+from .api import (Dissimilarity, GiniStress, Workspace, default_step, fit_host, gini_dist,
+                  gini_mds_fit, gini_pack, gini_rank, gini_stress, gini_stress_grad, tile_size,
+                  tiled_elems, workspace, workspace_size)
+
+__all__ = ["Dissimilarity", "GiniStress", "Workspace", "default_step", "fit_host", "gini_dist",
+           "gini_mds_fit", "gini_pack", "gini_rank", "gini_stress", "gini_stress_grad",
+           "tile_size", "tiled_elems", "workspace", "workspace_size"]

@@ -1,0 +1,86 @@
+"""ctypes loader for libginimds.so (the sm_103a CUDA library).
+
+Only argument marshalling lives here.  If the library is missing the import of
+any entry point raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libginimds.so")
+
+GINI_OK, GINI_EINVAL, GINI_ENONFINITE, GINI_EDEGENERATE, GINI_ENOMEM, GINI_ECUDA, GINI_ETIMEOUT = range(7)
+DTYPES = {"f32": 0, "bf16": 1, "bf16x2": 2, "fp8": 3}
+LAYOUTS = {"full": 0, "tiled": 1}
+OPS = {"rank": 0, "dist": 1, "stress": 2, "fit": 3}
+
+_c = ctypes
+_vp = _c.c_void_p
+_i64 = _c.c_int64
+
+
+class FitArgs(_c.Structure):
+    """Mirror of gini_fit_args in include/gini_mds.h."""
+    _fields_ = [
+        ("n", _i64), ("k", _c.c_int), ("nu", _c.c_double),
+        ("delta_dev", _vp), ("layout", _c.c_int), ("dtype", _c.c_int), ("ldd", _i64),
+        ("col_scale_dev", _vp), ("sum_delta2", _c.c_double), ("eta", _c.c_double),
+        ("iters", _c.c_int), ("polish_iters", _c.c_int), ("Y_dev", _vp),
+        ("history_dev", _vp), ("final_stress_dev", _vp),
+    ]
+
+
+# name -> (restype, argtypes); every symbol include/gini_mds.h declares.
+SIGNATURES = {
+    "gini_status_str": (_c.c_char_p, [_c.c_int]),
+    "gini_last_cuda_error": (_c.c_char_p, []),
+    "gini_version": (_c.c_int, []),
+    "gini_launch_count": (_c.c_uint64, []),
+    "gini_tile_size": (_c.c_int, []),
+    "gini_tiled_elems": (_i64, [_i64]),
+    "gini_workspace_size": (_c.c_size_t, [_c.c_int, _i64, _i64, _c.c_int, _c.c_int]),
+    "gini_check": (_c.c_int, [_vp, _vp]),
+    "gini_rank": (_c.c_int, [_vp, _i64, _i64, _i64, _vp, _vp, _c.c_size_t, _vp]),
+    "gini_dist": (_c.c_int, [_vp, _i64, _i64, _i64, _c.POINTER(_c.c_double), _c.c_int,
+                             _c.c_int, _c.c_int, _vp, _i64, _i64, _vp, _vp, _c.c_size_t, _vp]),
+    "gini_pack": (_c.c_int, [_vp, _i64, _i64, _c.c_int, _vp, _vp, _vp]),
+    "gini_stress_grad": (_c.c_int, [_vp, _i64, _c.c_int, _c.c_double, _vp, _c.c_int, _c.c_int,
+                                    _i64, _vp, _c.c_double, _vp, _vp, _vp, _c.c_size_t, _vp]),
+    "gini_mds_fit": (_c.c_int, [_c.POINTER(FitArgs), _vp, _c.c_size_t, _vp]),
+    "gini_default_step": (_c.c_double, [_i64, _c.c_int, _c.c_double, _c.c_double, _c.c_double]),
+}
+
+_lib = None
+
+
+class GiniError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        msg = lib().gini_status_str(status).decode()
+        if status == GINI_ECUDA:
+            msg += ": " + lib().gini_last_cuda_error().decode()
+        super().__init__(f"{where}: {msg}")
+        self.status = status
+
+
+def lib():
+    """The loaded library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                f"libginimds.so not found at {LIB_PATH}; build it with "
+                "`python -c 'import __graft_entry__ as g; g.build()'` (needs nvcc)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def check(status: int, where: str) -> None:
+    if status != GINI_OK:
+        raise GiniError(status, where)

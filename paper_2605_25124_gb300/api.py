@@ -1,0 +1,248 @@
+"""Torch-facing wrappers of the C ABI (same names as include/gini_mds.h).
+
+PyTorch supplies device memory and the current stream; every step of the
+computation runs in libginimds.so.  Nothing here computes the method.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+from typing import Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import DTYPES, LAYOUTS, OPS, check, lib
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _require_cuda(*ts):
+    for t in ts:
+        if t is not None and not t.is_cuda:
+            raise ValueError("libginimds works on CUDA tensors only")
+
+
+class Workspace:
+    """Caller-owned scratch memory for the library (zero-initialised once)."""
+
+    def __init__(self, device=None):
+        self.device = torch.device(device or "cuda")
+        self.buf = torch.zeros(256, dtype=torch.uint8, device=self.device)
+
+    def ensure(self, nbytes: int) -> torch.Tensor:
+        if self.buf.numel() < nbytes:
+            torch.cuda.current_stream(self.device).synchronize()
+            self.buf = torch.zeros(int(nbytes), dtype=torch.uint8, device=self.device)
+        return self.buf
+
+    def check(self, stream=None) -> None:
+        check(lib().gini_check(_ptr(self.buf), _stream(stream)), "gini_check")
+
+
+_ws_cache = {}
+
+
+def workspace(device=None) -> Workspace:
+    d = torch.device(device or "cuda")
+    key = (d.type, d.index if d.index is not None else torch.cuda.current_device())
+    if key not in _ws_cache:
+        _ws_cache[key] = Workspace(d)
+    return _ws_cache[key]
+
+
+def tile_size() -> int:
+    return int(lib().gini_tile_size())
+
+
+def tiled_elems(n: int) -> int:
+    return int(lib().gini_tiled_elems(int(n)))
+
+
+def workspace_size(op: str, n: int, m: int = 0, k: int = 0, iters: int = 0) -> int:
+    return int(lib().gini_workspace_size(OPS[op], int(n), int(m), int(k), int(iters)))
+
+
+def default_step(n: int, k: int, nu: float, sum_delta2: float, eta0: float = 1.0) -> float:
+    return float(lib().gini_default_step(int(n), int(k), float(nu), float(sum_delta2),
+                                         float(eta0)))
+
+
+def gini_rank(v: torch.Tensor, ws: Optional[Workspace] = None, check_errors: bool = True):
+    """Twice the midrank of every element of each row of v (nseg, m): int32."""
+    _require_cuda(v)
+    assert v.dtype == torch.float32 and v.dim() == 2 and v.stride(1) == 1
+    nseg, m = v.shape
+    out = torch.empty((nseg, m), dtype=torch.int32, device=v.device)
+    ws = ws or workspace(v.device)
+    buf = ws.ensure(workspace_size("rank", nseg, m))
+    st = lib().gini_rank(_ptr(v), nseg, m, v.stride(0), _ptr(out), _ptr(buf), buf.numel(),
+                         _stream())
+    check(st, "gini_rank")
+    if check_errors:
+        ws.check()
+    return out
+
+
+@dataclass
+class Dissimilarity:
+    """A dissimilarity matrix as stored on the device."""
+    data: torch.Tensor             # FULL: (n, n) f32; TILED: flat storage of one matrix
+    n: int
+    layout: str                    # "full" | "tiled"
+    dtype: str                     # "f32" | "bf16" | "bf16x2" | "fp8"
+    sum_delta2: float
+    col_scale: Optional[torch.Tensor] = None
+
+    @property
+    def ldd(self) -> int:
+        return self.data.stride(0) if self.layout == "full" else 0
+
+
+_TORCH_DT = {"f32": torch.float32, "bf16": torch.bfloat16, "bf16x2": torch.bfloat16,
+             "fp8": torch.uint8}
+
+
+def gini_dist(X: torch.Tensor, nus: Sequence[float], layout: str = "full", dtype: str = "f32",
+              ws: Optional[Workspace] = None, check_errors: bool = True):
+    """Dissimilarity matrices for every nu: returns (list of Dissimilarity,
+    sum_delta2 tensor (n_nu,) float64 on the device)."""
+    _require_cuda(X)
+    assert X.dtype == torch.float32 and X.dim() == 2 and X.stride(1) == 1
+    n, p = X.shape
+    nus = [float(v) for v in nus]
+    n_nu = len(nus)
+    if layout == "full":
+        out = torch.empty((n_nu, n, n), dtype=torch.float32, device=X.device)
+        stride = n * n
+    else:
+        planes = 2 if dtype == "bf16x2" else 1
+        stride = planes * tiled_elems(n)
+        out = torch.empty((n_nu, stride), dtype=_TORCH_DT[dtype], device=X.device)
+    sd2 = torch.zeros(n_nu, dtype=torch.float64, device=X.device)
+    ws = ws or workspace(X.device)
+    buf = ws.ensure(workspace_size("dist", n, p))
+    nu_arr = (ctypes.c_double * n_nu)(*nus)
+    st = lib().gini_dist(_ptr(X), n, p, X.stride(0), nu_arr, n_nu, LAYOUTS[layout],
+                         DTYPES[dtype], _ptr(out), n, stride, _ptr(sd2), _ptr(buf), buf.numel(),
+                         _stream())
+    check(st, "gini_dist")
+    if check_errors:
+        ws.check()
+    sums = sd2.cpu().tolist()
+    mats = [Dissimilarity(out[q], n, layout, dtype, sums[q]) for q in range(n_nu)]
+    return mats, sd2
+
+
+def gini_pack(D: Dissimilarity, dtype: str) -> Dissimilarity:
+    """FULL f32 -> TILED of the given dtype (FP8 with per-column scales)."""
+    assert D.layout == "full" and D.dtype == "f32"
+    n = D.n
+    planes = 2 if dtype == "bf16x2" else 1
+    out = torch.empty(planes * tiled_elems(n), dtype=_TORCH_DT[dtype], device=D.data.device)
+    scale = torch.empty(n, dtype=torch.float32, device=D.data.device) if dtype == "fp8" else None
+    st = lib().gini_pack(_ptr(D.data), n, D.data.stride(0), DTYPES[dtype], _ptr(out),
+                         _ptr(scale), _stream())
+    check(st, "gini_pack")
+    return Dissimilarity(out, n, "tiled", dtype, D.sum_delta2, scale)
+
+
+def gini_stress_grad(Y: torch.Tensor, nu: float, D: Dissimilarity, grad: bool = True,
+                     ws: Optional[Workspace] = None, check_errors: bool = True):
+    """(S as a float64 0-d tensor, dS/dY or None)."""
+    _require_cuda(Y)
+    assert Y.dtype == torch.float32 and Y.is_contiguous()
+    n, k = Y.shape
+    stress = torch.empty((), dtype=torch.float64, device=Y.device)
+    g = torch.empty_like(Y) if grad else None
+    ws = ws or workspace(Y.device)
+    buf = ws.ensure(workspace_size("stress", n, 0, k))
+    st = lib().gini_stress_grad(_ptr(Y), n, k, float(nu), _ptr(D.data), LAYOUTS[D.layout],
+                                DTYPES[D.dtype], D.ldd, _ptr(D.col_scale), D.sum_delta2,
+                                _ptr(stress), _ptr(g), _ptr(buf), buf.numel(), _stream())
+    check(st, "gini_stress_grad")
+    if check_errors:
+        ws.check()
+    return stress, g
+
+
+def gini_mds_fit(Y0: torch.Tensor, nu: float, D: Dissimilarity, eta: float, iters: int,
+                 polish_iters: int = 0, history: bool = True, ws: Optional[Workspace] = None,
+                 check_errors: bool = True, out: Optional[torch.Tensor] = None):
+    """Fixed-step GD on the normalized stress; returns (Y_T, history or None, S(Y_T))."""
+    _require_cuda(Y0)
+    n, k = Y0.shape
+    Y = out if out is not None else Y0.clone()
+    if out is not None:
+        out.copy_(Y0)
+    hist = torch.empty(iters + 1, dtype=torch.float64, device=Y0.device) if history else None
+    final = torch.empty((), dtype=torch.float64, device=Y0.device)
+    ws = ws or workspace(Y0.device)
+    buf = ws.ensure(workspace_size("fit", n, 0, k, iters))
+    a = _lib.FitArgs(n=n, k=k, nu=float(nu), delta_dev=D.data.data_ptr(),
+                     layout=LAYOUTS[D.layout], dtype=DTYPES[D.dtype], ldd=D.ldd,
+                     col_scale_dev=(D.col_scale.data_ptr() if D.col_scale is not None else None),
+                     sum_delta2=D.sum_delta2, eta=float(eta), iters=int(iters),
+                     polish_iters=int(polish_iters), Y_dev=Y.data_ptr(),
+                     history_dev=(hist.data_ptr() if hist is not None else None),
+                     final_stress_dev=final.data_ptr())
+    st = lib().gini_mds_fit(ctypes.byref(a), _ptr(buf), buf.numel(), _stream())
+    check(st, "gini_mds_fit")
+    if check_errors:
+        ws.check()
+    return Y, hist, final
+
+
+class GiniStress(torch.autograd.Function):
+    """S(Y) = sum_{i<j} (Dbar(y_i, y_j) - delta_ij)^2 / sum_delta2 as an autograd op.
+
+    The forward pass runs the fused stress+adjoint kernel when Y needs a
+    gradient and keeps only dS/dY (n x k); nothing n x n is stored.  The
+    backward pass scales it by the incoming gradient.
+    """
+
+    @staticmethod
+    def forward(ctx, Y, nu, D):
+        S, g = gini_stress_grad(Y.detach().contiguous(), nu, D, grad=Y.requires_grad)
+        ctx.save_for_backward(g if g is not None else torch.empty(0, device=Y.device))
+        return S
+
+    @staticmethod
+    def backward(ctx, gS):
+        (g,) = ctx.saved_tensors
+        return (gS.to(g.dtype) * g), None, None
+
+
+def gini_stress(Y: torch.Tensor, nu: float, D: Dissimilarity) -> torch.Tensor:
+    return GiniStress.apply(Y, nu, D)
+
+
+def fit_host(X: np.ndarray, nu: float, k: int, iters: int, Y0: np.ndarray, eta0: float = 1.0,
+             dtype: str = "bf16x2", polish_iters: int = 20, device="cuda"):
+    """End-to-end from host arrays: copy X and Y0 in, build Delta, fit, copy
+    Y_T and S(Y_T) out.  Returns (Y_T as numpy, S(Y_T), sum_delta2)."""
+    dev = torch.device(device)
+    Xh = torch.from_numpy(np.ascontiguousarray(X, dtype=np.float32)).pin_memory()
+    Yh = torch.from_numpy(np.ascontiguousarray(Y0, dtype=np.float32)).pin_memory()
+    Xd = Xh.to(dev, non_blocking=True)
+    Yd = Yh.to(dev, non_blocking=True)
+    layout = "full" if dtype == "full" else "tiled"
+    mats, _ = gini_dist(Xd, [nu], layout=layout, dtype=("f32" if dtype == "full" else dtype),
+                        check_errors=False)
+    D = mats[0]
+    eta = default_step(X.shape[0], k, nu, D.sum_delta2, eta0)
+    Y, _, final = gini_mds_fit(Yd, nu, D, eta, iters, polish_iters=polish_iters, history=False,
+                               check_errors=False)
+    Yout = torch.empty(Y.shape, dtype=torch.float32, pin_memory=True)
+    Yout.copy_(Y, non_blocking=True)
+    fin = final.to("cpu", non_blocking=True)
+    torch.cuda.current_stream().synchronize()
+    return Yout.numpy(), float(fin), D.sum_delta2

@@ -1,0 +1,169 @@
+// Host-side C ABI helpers of libginimds and the FULL -> TILED pack kernels.
+#include <math.h>
+#include <string.h>
+
+#include <atomic>
+
+#include "common.cuh"
+
+using namespace gini;
+
+static thread_local char g_cuda_err[256] = "";
+static std::atomic<uint64_t> g_launches{0};
+
+extern "C" void gini_count_launch(unsigned n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+extern "C" uint64_t gini_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+extern "C" size_t gini_iter_ws_bytes(int64_t n, int k, int nacc);
+
+extern "C" void gini_set_cuda_error(cudaError_t e) {
+  strncpy(g_cuda_err, cudaGetErrorString(e), sizeof(g_cuda_err) - 1);
+  g_cuda_err[sizeof(g_cuda_err) - 1] = 0;
+}
+
+extern "C" const char* gini_last_cuda_error(void) { return g_cuda_err; }
+
+extern "C" const char* gini_status_str(int status) {
+  switch (status) {
+    case GINI_OK: return "GINI_OK";
+    case GINI_EINVAL: return "GINI_EINVAL: invalid argument";
+    case GINI_ENONFINITE: return "GINI_ENONFINITE: NaN or Inf in the input";
+    case GINI_EDEGENERATE: return "GINI_EDEGENERATE: sum of squared dissimilarities is zero";
+    case GINI_ENOMEM: return "GINI_ENOMEM: workspace too small";
+    case GINI_ECUDA: return "GINI_ECUDA: CUDA runtime error";
+    case GINI_ETIMEOUT: return "GINI_ETIMEOUT: bounded device wait expired";
+    default: return "unknown gini status";
+  }
+}
+
+extern "C" int gini_version(void) { return 1; }
+
+extern "C" int gini_tile_size(void) { return TILE; }
+
+extern "C" int64_t gini_tiled_elems(int64_t n) {
+  const int64_t T = tiles_1d(n);
+  return T * (T + 1) / 2 * (int64_t)TILE * TILE;
+}
+
+extern "C" size_t gini_workspace_size(int op, int64_t n, int64_t m, int k, int iters) {
+  switch (op) {
+    case GINI_OP_RANK: return WS_HEADER;
+    case GINI_OP_DIST: {
+      const int64_t mm = m < 1 ? 1 : m;
+      return WS_HEADER + (size_t)8 * (size_t)(2 * mm - 1) * sizeof(float);
+    }
+    case GINI_OP_STRESS: return gini_iter_ws_bytes(n, k < 2 ? 2 : k, 1);
+    case GINI_OP_FIT: return gini_iter_ws_bytes(n, k < 2 ? 2 : k, (iters < 0 ? 0 : iters) + 1);
+    default: return 0;
+  }
+}
+
+extern "C" int gini_check(void* ws, void* stream) {
+  if (!ws) return GINI_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaStreamSynchronize(s);
+  unsigned word = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&word, ws, sizeof(word), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && word) e = cudaMemset(ws, 0, sizeof(word));
+  if (e != cudaSuccess) { gini_set_cuda_error(e); return GINI_ECUDA; }
+  if (word & ERR_TIMEOUT) return GINI_ETIMEOUT;
+  if (word & ERR_NONFINITE) return GINI_ENONFINITE;
+  return GINI_OK;
+}
+
+extern "C" double gini_default_step(int64_t n, int k, double nu, double sum_delta2, double eta0) {
+  if (n < 2 || k < 2 || !(nu > 1.0)) return 0.0;
+  const double wmax = pow((double)(k - 1) / (double)k, nu - 1.0);
+  const double g = 0.5 * (double)k * wmax;
+  return eta0 * sum_delta2 / (2.0 * (double)(n - 1) * (double)k * g * g);
+}
+
+// ----------------------------------------------------------------- pack ----
+
+// Column maxima of |delta_ij| over i < j (as float bits: values are >= 0, so
+// integer max of the bit patterns is the float max).
+__global__ void k_colmax(const float* __restrict__ D, int64_t n, int64_t ldd,
+                         unsigned* __restrict__ colmax) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const int64_t i0 = (int64_t)blockIdx.y * 256;
+  unsigned m = 0;
+  for (int64_t i = i0; i < i0 + 256 && i < j; ++i) {
+    const float v = fabsf(D[i * ldd + j]);
+    m = max(m, __float_as_uint(v));
+  }
+  if (m) atomicMax(colmax + j, m);
+}
+
+__global__ void k_scale_from_max(unsigned* colmax_bits, int64_t n) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const float mx = __uint_as_float(colmax_bits[j]);
+  const float sc = mx > 0.f ? mx / 448.f : 1.f;
+  reinterpret_cast<float*>(colmax_bits)[j] = sc;
+}
+
+// One thread per stored element of one tile row chunk.
+template <int DT>
+__global__ void k_pack(const float* __restrict__ D, int64_t n, int64_t ldd, int64_t T,
+                       int64_t plane, void* __restrict__ out, const float* __restrict__ scale) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t ntile = T * (T + 1) / 2;
+  if (e >= ntile * TILE * TILE) return;
+  const int64_t t = e / (TILE * TILE);
+  const int rc = (int)(e % (TILE * TILE));
+  int I, J;
+  tile_decode(t, T, I, J);
+  const int64_t i = (int64_t)I * TILE + rc / TILE, j = (int64_t)J * TILE + rc % TILE;
+  const float v = (i < n && j < n && i < j) ? D[i * ldd + j] : 0.f;
+  if (DT == GINI_F32) {
+    reinterpret_cast<float*>(out)[e] = v;
+  } else if (DT == GINI_BF16) {
+    reinterpret_cast<__nv_bfloat16*>(out)[e] = __float2bfloat16_rn(v);
+  } else if (DT == GINI_BF16X2) {
+    const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+    reinterpret_cast<__nv_bfloat16*>(out)[e] = hi;
+    reinterpret_cast<__nv_bfloat16*>(out)[plane + e] = __float2bfloat16_rn(v - __bfloat162float(hi));
+  } else {
+    const float sc = (j < n) ? scale[j] : 1.f;
+    reinterpret_cast<__nv_fp8_storage_t*>(out)[e] =
+        __nv_cvt_float_to_fp8(v / sc, __NV_SATFINITE, __NV_E4M3);
+  }
+}
+
+extern "C" int gini_pack(const float* delta_full_dev, int64_t n, int64_t ldd, int dtype,
+                         void* packed_dev, float* col_scale_dev, void* stream) {
+  if (!delta_full_dev || !packed_dev || n < 2 || ldd < n || n > ((int64_t)1 << 31))
+    return GINI_EINVAL;
+  if (dtype < GINI_F32 || dtype > GINI_FP8E4M3) return GINI_EINVAL;
+  if (dtype == GINI_FP8E4M3 && !col_scale_dev) return GINI_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t T = tiles_1d(n);
+  const int64_t plane = gini_tiled_elems(n);
+  cudaError_t e = cudaSuccess;
+  if (dtype == GINI_FP8E4M3) {
+    e = cudaMemsetAsync(col_scale_dev, 0, sizeof(float) * n, s);
+    if (e == cudaSuccess) {
+      dim3 g((unsigned)((n + 255) / 256), (unsigned)((n + 255) / 256));
+      gini_count_launch(2);
+      k_colmax<<<g, 256, 0, s>>>(delta_full_dev, n, ldd, reinterpret_cast<unsigned*>(col_scale_dev));
+      k_scale_from_max<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
+          reinterpret_cast<unsigned*>(col_scale_dev), n);
+      e = cudaGetLastError();
+    }
+  }
+  if (e == cudaSuccess) {
+    const unsigned blocks = (unsigned)((plane + 255) / 256);
+    gini_count_launch(1);
+    switch (dtype) {
+      case GINI_F32: k_pack<GINI_F32><<<blocks, 256, 0, s>>>(delta_full_dev, n, ldd, T, plane, packed_dev, col_scale_dev); break;
+      case GINI_BF16: k_pack<GINI_BF16><<<blocks, 256, 0, s>>>(delta_full_dev, n, ldd, T, plane, packed_dev, col_scale_dev); break;
+      case GINI_BF16X2: k_pack<GINI_BF16X2><<<blocks, 256, 0, s>>>(delta_full_dev, n, ldd, T, plane, packed_dev, col_scale_dev); break;
+      default: k_pack<GINI_FP8E4M3><<<blocks, 256, 0, s>>>(delta_full_dev, n, ldd, T, plane, packed_dev, col_scale_dev); break;
+    }
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) { gini_set_cuda_error(e); return GINI_ECUDA; }
+  return GINI_OK;
+}

@@ -1,0 +1,77 @@
+// Shared device helpers of libginimds (sm_103a).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gini_mds.h"
+
+extern "C" void gini_count_launch(unsigned n);
+
+namespace gini {
+
+constexpr unsigned FULL_MASK = 0xffffffffu;
+constexpr int TILE = 128;  // edge B of the tiled triangle layout
+
+// Device-side error bits, OR-ed into the first word of the workspace.
+constexpr unsigned ERR_NONFINITE = 1u;
+constexpr unsigned ERR_TIMEOUT = 2u;
+
+// The first 256 bytes of every workspace hold the error word.
+constexpr size_t WS_HEADER = 256;
+
+__device__ __forceinline__ void raise_error(unsigned* err, unsigned bit) {
+  if (err) atomicOr(err, bit);
+}
+
+// Number of tiles along one edge for n points.
+__host__ __device__ __forceinline__ int64_t tiles_1d(int64_t n) { return (n + TILE - 1) / TILE; }
+
+// Linear index of tile (I, J), I <= J, in the row-major upper-triangular order.
+__host__ __device__ __forceinline__ int64_t tile_offset(int64_t I, int64_t J, int64_t T) {
+  return I * T - I * (I - 1) / 2 + (J - I);
+}
+
+// Inverse of tile_offset: the tile (I, J) with linear index t.
+__device__ __forceinline__ void tile_decode(int64_t t, int64_t T, int& I, int& J) {
+  double b = 2.0 * (double)T + 1.0;
+  int64_t i = (int64_t)((b - sqrt(b * b - 8.0 * (double)t)) * 0.5);
+  if (i < 0) i = 0;
+  if (i > T - 1) i = T - 1;
+  while (i > 0 && tile_offset(i, i, T) > t) --i;
+  while (i + 1 < T && tile_offset(i + 1, i + 1, T) <= t) ++i;
+  I = (int)i;
+  J = (int)(t - tile_offset(i, i, T) + i);
+}
+
+// Offset (in elements) of delta(i, j), i < j, in one plane of the tiled layout.
+__device__ __forceinline__ int64_t tiled_index(int64_t i, int64_t j, int64_t T) {
+  int64_t I = i / TILE, J = j / TILE;
+  return tile_offset(I, J, T) * (int64_t)(TILE * TILE) + (i % TILE) * TILE + (j % TILE);
+}
+
+// Exact difference a - b = hi + lo for floats (TwoSum, Knuth).  Exact as long
+// as nothing underflows.
+__device__ __forceinline__ float2 two_diff(float a, float b) {
+  float s = __fsub_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  float lo = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(-b, bb));
+  return make_float2(s, lo);
+}
+
+// Sign of (p.hi + p.lo) - (q.hi + q.lo) for two exact pairs produced by
+// two_diff (|lo| <= ulp(hi)/2).  Rounding is monotone, so different hi parts
+// already order the exact values; equal hi parts are ordered by lo.
+__device__ __forceinline__ int exact_cmp(float2 p, float2 q) {
+  if (p.x != q.x) return p.x < q.x ? -1 : 1;
+  if (p.y != q.y) return p.y < q.y ? -1 : 1;
+  return 0;
+}
+
+__device__ __forceinline__ float bf16_bits_to_float(uint32_t h16) {
+  return __uint_as_float(h16 << 16);
+}
+
+}  // namespace gini

@@ -1,0 +1,312 @@
+// Dissimilarity matrix build: Delta_q(i, j) = Dbar_{G,nu_q}(x_i, x_j)
+// (Section III-B, symmetrized generalized Gini pseudo-distance; Algorithm 1).
+//
+// Per pair (i, j), i < j, one segment of L lanes:
+//   z = x_i - x_j                         (FP32, E registers per lane)
+//   sort z ascending                      (register bitonic network)
+//   2R(pos) = first + last position of pos's tie run, + 2   (midranks)
+//   delta_q = sum_pos z(pos) * T_q[2R - 2],  T_q = (d/2) W_{d,nu_q}
+// One sort serves every nu.  For a single nu = 2 the weight is affine in the
+// rank, (d/2) W = R - (d+1)/2, so a tie run's midrank weight equals the mean of
+// its positional weights and the run bookkeeping is skipped (exactly equal).
+//
+// Work split: CTA = 8 warps = 8 consecutive rows i; blockIdx.x picks a block
+// of CB columns j.  A warp keeps x_i in registers and walks its columns, each
+// of the 32/L segments taking every (32/L)-th j.  X is read through L2 (a row
+// is a few KB; the per-pair compute dwarfs the traffic).
+#include <math.h>
+#include <stdio.h>
+
+#include <vector>
+
+#include "common.cuh"
+#include "sortnet.cuh"
+
+namespace gini {
+
+constexpr int DIST_WARPS = 8;
+constexpr int NU_MAX = 8;
+
+struct DistParams {
+  const float* X;
+  int64_t n, m, ldx;
+  int n_nu;
+  const float* wtab;  // n_nu x (2m - 1), T_q[idx], idx = first + last position
+  int layout, dtype;
+  void* out;
+  int64_t ldd, nu_stride;
+  int64_t tiles;      // tiles along one edge (TILED)
+  int64_t plane;      // elements in one plane (TILED)
+  double* sum_delta2;
+  unsigned* err;
+  int cb;             // columns per CTA
+};
+
+__device__ __forceinline__ void store_delta(const DistParams& P, int q, int64_t i, int64_t j,
+                                            float d) {
+  if (P.layout == GINI_LAYOUT_FULL) {
+    float* o = reinterpret_cast<float*>(P.out) + (int64_t)q * P.nu_stride;
+    o[i * P.ldd + j] = d;
+    o[j * P.ldd + i] = d;
+    return;
+  }
+  const int64_t idx = (int64_t)q * P.nu_stride + tiled_index(i, j, P.tiles);
+  if (P.dtype == GINI_F32) {
+    reinterpret_cast<float*>(P.out)[idx] = d;
+  } else if (P.dtype == GINI_BF16) {
+    reinterpret_cast<__nv_bfloat16*>(P.out)[idx] = __float2bfloat16_rn(d);
+  } else {  // GINI_BF16X2
+    __nv_bfloat16 hi = __float2bfloat16_rn(d);
+    __nv_bfloat16 lo = __float2bfloat16_rn(d - __bfloat162float(hi));
+    reinterpret_cast<__nv_bfloat16*>(P.out)[idx] = hi;
+    reinterpret_cast<__nv_bfloat16*>(P.out)[idx + P.plane] = lo;
+  }
+}
+
+// Skewed shared-memory address of table entry idx: sorted positions of one
+// lane are E apart, so idx ~ 2*E*ls + 2t; adding idx / (2E) spreads the lanes
+// of a segment over distinct banks.
+template <int E>
+__device__ __forceinline__ int tab_addr(int idx) {
+  return idx + (idx / (2 * E));
+}
+
+template <int E, int L, bool AFFINE>
+__global__ void __launch_bounds__(DIST_WARPS * 32)
+k_dist(const DistParams P) {
+  constexpr int G = 32 / L;
+  constexpr int NQ = AFFINE ? 1 : NU_MAX;  // nu slots carried in registers
+  extern __shared__ float s_tab[];  // n_nu x tab_stride
+  __shared__ double s_red[DIST_WARPS][NU_MAX];
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int seg = lane / L, ls = lane % L;
+  const int64_t row0 = (int64_t)blockIdx.y * DIST_WARPS;
+  const int64_t col0 = (int64_t)blockIdx.x * P.cb;
+  // Nothing above the diagonal in this block (uniform exit, before any barrier).
+  if (col0 + P.cb - 1 <= row0 || row0 >= P.n - 1) return;
+
+  const int m = (int)P.m;
+  const int tab_n = 2 * m - 1;
+  const int tab_stride = tab_addr<E>(tab_n - 1) + 1;
+  if (!AFFINE) {
+    for (int q = 0; q < P.n_nu; ++q)
+      for (int idx = threadIdx.x; idx < tab_n; idx += blockDim.x)
+        s_tab[q * tab_stride + tab_addr<E>(idx)] = P.wtab[(int64_t)q * tab_n + idx];
+    __syncthreads();
+  }
+
+  const int64_t i = row0 + warp;
+  const bool row_ok = i < P.n - 1;
+  float xi[E];
+#pragma unroll
+  for (int t = 0; t < E; ++t) {
+    const int e = t * L + ls;
+    xi[t] = (row_ok && e < m) ? __ldg(P.X + i * P.ldx + e) : 0.f;
+  }
+
+  double sd2[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) sd2[q] = 0.0;
+
+  const float mid = 0.5f * (float)(m - 1);
+  for (int64_t jb = col0; jb < col0 + P.cb; jb += G) {
+    const int64_t j = jb + seg;
+    const bool active = row_ok && j > i && j < P.n;
+    if (!__any_sync(FULL_MASK, active)) continue;
+    float v[E];
+#pragma unroll
+    for (int t = 0; t < E; ++t) {
+      const int e = t * L + ls;
+      float xj = (active && e < m) ? __ldg(P.X + j * P.ldx + e) : 0.f;
+      v[t] = (e < m) ? xi[t] - xj : __int_as_float(0x7f800000);  // pad with +inf
+    }
+    seg_bitonic_sort<E, L>(v, ls);
+
+    float acc[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) acc[q] = 0.f;
+    const int pos0 = E * ls;
+    if (AFFINE) {
+      // nu = 2: (d/2) W(R) = R - (d+1)/2 at position pos (0-based): pos - (d-1)/2
+#pragma unroll
+      for (int t = 0; t < E; ++t) {
+        const int pos = pos0 + t;
+        if (pos < m) acc[0] = fmaf(v[t], (float)pos - mid, acc[0]);
+      }
+    } else {
+      int run_lo[E];
+      int carry_e;
+      bool cont_right;
+      seg_runs<E, L>(v, ls, [](float a, float b) { return a == b; }, run_lo, carry_e, cont_right);
+      int e = cont_right ? carry_e : pos0 + E - 1;
+#pragma unroll
+      for (int t = E - 1; t >= 0; --t) {
+        if (t < E - 1) e = (v[t] == v[t + 1]) ? e : pos0 + t;
+        if (pos0 + t < m) {
+          // a value equal to the +inf padding (an overflowed difference) would
+          // extend its run into the padding: keep the run end inside [0, m)
+          const int a = tab_addr<E>(run_lo[t] + min(e, m - 1));
+#pragma unroll
+          for (int q = 0; q < NQ; ++q)
+            if (q < P.n_nu) acc[q] = fmaf(v[t], s_tab[q * tab_stride + a], acc[q]);
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      if (q < P.n_nu) {
+#pragma unroll
+        for (int o = L / 2; o >= 1; o >>= 1) acc[q] += __shfl_xor_sync(FULL_MASK, acc[q], o);
+      }
+    }
+    if (active && ls == 0) {
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {
+        if (q < P.n_nu) {
+          store_delta(P, q, i, j, acc[q]);
+          sd2[q] += (double)acc[q] * (double)acc[q];
+        }
+      }
+    }
+  }
+
+  // sum_{i<j} delta^2: warp, then CTA, then one FP64 atomic per nu.
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) sd2[q] += __shfl_xor_sync(FULL_MASK, sd2[q], o);
+  }
+  if (lane == 0)
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) s_red[warp][q] = sd2[q];
+  __syncthreads();
+  if (threadIdx.x < P.n_nu && P.sum_delta2) {
+    double s = 0.0;
+    for (int w = 0; w < DIST_WARPS; ++w) s += s_red[w][threadIdx.x];
+    if (s != 0.0) atomicAdd(P.sum_delta2 + threadIdx.x, s);
+  }
+}
+
+__global__ void k_check_finite(const float* X, int64_t n, int64_t m, int64_t ld, unsigned* err) {
+  bool bad = false;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n * m;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / m, c = e % m;
+    bad |= !isfinite(X[r * ld + c]);
+  }
+  if (__any_sync(FULL_MASK, bad) && (threadIdx.x & 31) == 0) raise_error(err, ERR_NONFINITE);
+}
+
+__global__ void k_zero_diag(float* D, int64_t n, int64_t ldd, int64_t nu_stride, int n_nu) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n)
+    for (int q = 0; q < n_nu; ++q) D[(int64_t)q * nu_stride + i * ldd + i] = 0.f;
+}
+
+template <int E, int L, bool AFFINE>
+static cudaError_t launch_dist(const DistParams& P, cudaStream_t s) {
+  const int m = (int)P.m;
+  const int tab_n = 2 * m - 1;
+  const int tab_stride = tab_n - 1 + (tab_n - 1) / (2 * E) + 1;
+  const size_t smem = AFFINE ? 0 : (size_t)P.n_nu * tab_stride * sizeof(float);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_dist<E, L, AFFINE>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  DistParams Q = P;
+  constexpr int G = 32 / L;
+  Q.cb = G * (L >= 8 ? 16 : 4);  // columns per CTA: several passes per warp
+  dim3 grid((unsigned)((P.n + Q.cb - 1) / Q.cb), (unsigned)((P.n + DIST_WARPS - 1) / DIST_WARPS));
+  gini_count_launch(1);
+  k_dist<E, L, AFFINE><<<grid, DIST_WARPS * 32, smem, s>>>(Q);
+  return cudaGetLastError();
+}
+
+template <bool AFFINE>
+static cudaError_t dispatch_dist(const DistParams& P, cudaStream_t s) {
+  const int64_t m = P.m;
+  if (m <= 4) return launch_dist<4, 1, AFFINE>(P, s);
+  if (m <= 8) return launch_dist<8, 1, AFFINE>(P, s);
+  if (m <= 16) return launch_dist<16, 1, AFFINE>(P, s);
+  if (m <= 32) return launch_dist<32, 1, AFFINE>(P, s);
+  if (m <= 64) return launch_dist<32, 2, AFFINE>(P, s);
+  if (m <= 128) return launch_dist<32, 4, AFFINE>(P, s);
+  if (m <= 256) return launch_dist<32, 8, AFFINE>(P, s);
+  if (m <= 512) return launch_dist<32, 16, AFFINE>(P, s);
+  return launch_dist<32, 32, AFFINE>(P, s);
+}
+
+}  // namespace gini
+
+using namespace gini;
+
+extern "C" void gini_set_cuda_error(cudaError_t e);
+
+extern "C" int gini_dist(const float* X_dev, int64_t n, int64_t p, int64_t ldx,
+                         const double* nu_host, int n_nu, int layout, int dtype, void* delta_dev,
+                         int64_t ldd, int64_t nu_stride, double* sum_delta2_dev, void* ws,
+                         size_t ws_bytes, void* stream) {
+  if (!X_dev || !delta_dev || !nu_host || !ws) return GINI_EINVAL;
+  if (n < 2 || p < 1 || p > 1024 || ldx < p || n_nu < 1 || n_nu > NU_MAX) return GINI_EINVAL;
+  if (n > (int64_t)65535 * DIST_WARPS) return GINI_EINVAL;  // grid.y = ceil(n / 8)
+  for (int q = 0; q < n_nu; ++q)
+    if (!(nu_host[q] > 1.0) || !isfinite(nu_host[q])) return GINI_EINVAL;
+  if (layout == GINI_LAYOUT_FULL) {
+    if (dtype != GINI_F32 || ldd < n) return GINI_EINVAL;
+    if (n_nu > 1 && nu_stride < ldd * n) return GINI_EINVAL;
+  } else if (layout == GINI_LAYOUT_TILED) {
+    if (dtype != GINI_F32 && dtype != GINI_BF16 && dtype != GINI_BF16X2) return GINI_EINVAL;
+    const int64_t plane = gini_tiled_elems(n);
+    if (n_nu > 1 && nu_stride < plane * (dtype == GINI_BF16X2 ? 2 : 1)) return GINI_EINVAL;
+  } else {
+    return GINI_EINVAL;
+  }
+  if (ws_bytes < gini_workspace_size(GINI_OP_DIST, n, p, 0, 0)) return GINI_ENOMEM;
+
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned* err = reinterpret_cast<unsigned*>(ws);
+  float* wtab = reinterpret_cast<float*>(reinterpret_cast<char*>(ws) + WS_HEADER);
+  const bool affine = (n_nu == 1 && nu_host[0] == 2.0);
+  const int tab_n = (int)(2 * p - 1);
+  if (!affine) {
+    // T_q[idx] = (d/2) W_{d,nu_q}((idx + 2)/2), W(R) = ((R-1)/d)^{nu-1} - ((d-R)/d)^{nu-1}
+    std::vector<float> tab((size_t)n_nu * tab_n);
+    const double d = (double)p;
+    for (int q = 0; q < n_nu; ++q)
+      for (int idx = 0; idx < tab_n; ++idx) {
+        const double R = (idx + 2) / 2.0;
+        const double W = pow((R - 1.0) / d, nu_host[q] - 1.0) - pow((d - R) / d, nu_host[q] - 1.0);
+        tab[(size_t)q * tab_n + idx] = (float)(0.5 * d * W);
+      }
+    // From pageable memory the copy is staged before cudaMemcpyAsync returns,
+    // so `tab` may be released right after the call.
+    cudaError_t e = cudaMemcpyAsync(wtab, tab.data(), tab.size() * sizeof(float),
+                                    cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) { gini_set_cuda_error(e); return GINI_ECUDA; }
+  }
+  cudaError_t e = cudaSuccess;
+  if (sum_delta2_dev) e = cudaMemsetAsync(sum_delta2_dev, 0, sizeof(double) * n_nu, s);
+  if (e == cudaSuccess) {
+    gini_count_launch(1);
+    k_check_finite<<<296, 256, 0, s>>>(X_dev, n, p, ldx, err);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess && layout == GINI_LAYOUT_FULL) {
+    gini_count_launch(1);
+    k_zero_diag<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((float*)delta_dev, n, ldd,
+                                                           nu_stride, n_nu);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) {
+    DistParams P{};
+    P.X = X_dev; P.n = n; P.m = p; P.ldx = ldx; P.n_nu = n_nu; P.wtab = wtab;
+    P.layout = layout; P.dtype = dtype; P.out = delta_dev; P.ldd = ldd; P.nu_stride = nu_stride;
+    P.tiles = tiles_1d(n); P.plane = gini_tiled_elems(n);
+    P.sum_delta2 = sum_delta2_dev; P.err = err;
+    e = affine ? dispatch_dist<true>(P, s) : dispatch_dist<false>(P, s);
+  }
+  if (e != cudaSuccess) { gini_set_cuda_error(e); return GINI_ECUDA; }
+  return GINI_OK;
+}

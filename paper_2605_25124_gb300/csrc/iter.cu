@@ -1,0 +1,776 @@
+// Kruskal stress and its adjoint for an embedding Y (n x k) under the Gini
+// pseudo-distance, and the fixed-step gradient-descent fit (Section IV-B;
+// Algorithm 1, "Run MDS").
+//
+//   d_ij = Dbar_{G,nu}(y_i, y_j) = sum_c z_c T[2R_c - 2],  z = y_i - y_j,
+//          T = (k/2) W_{k,nu}, R_c the midrank of z_c among the k components;
+//   r_ij = d_ij - delta_ij,  S = sum_{i<j} r_ij^2 / sum_delta2;
+//   dS/dy_i = 2/sum_delta2 * sum_{j != i} r_ij T[2R(y_i - y_j) - 2]  (ranks fixed).
+//
+// Ranks of z are decided exactly: z_a < z_b  <=>  (y_ia - y_ib) < (y_ja - y_jb),
+// and each point carries its within-point differences y_ia - y_ib as exact
+// TwoSum pairs (computed once per iteration), so the comparison of two points
+// is exact.  For k = 2 this reduces to u_i = y_i0 - y_i1 and
+//   d_ij = 2^{1-nu} |u_i - u_j|,  dd_ij/dy_i = 2^{1-nu} sign(u_i - u_j) (1, -1),
+// with sign 0 at an exact tie (W(3/2) = 0 for k = 2).
+//
+// Two forms:
+//   plain  (GINI_LAYOUT_FULL, F32): a forward kernel over i<j for S, then an
+//          adjoint kernel over all ordered pairs for dS/dY (each recomputes d).
+//   fused  (GINI_LAYOUT_TILED, any dtype): one pass over the stored triangle of
+//          B x B tiles; each element feeds the stress, its row's gradient and
+//          its column's gradient (d_ji = d_ij, antisymmetric derivative).
+#include <math.h>
+
+#include "common.cuh"
+
+namespace gini {
+
+constexpr int KMAX = 8;
+constexpr int FUSED_THREADS = 256;  // 8 warps; a warp owns 16 rows of a 128 x 128 tile
+
+struct PairTab {
+  float c2;               // k = 2: 2^{1-nu}
+  float w[2 * KMAX - 1];  // (k/2) W_{k,nu}(R) at 2R - 2 = 0 .. 2k - 2
+};
+
+struct IterParams {
+  int64_t n;
+  const float2* P;  // per point: k = 2 -> u_i as (hi, lo); else the k(k-1)/2 pairs y_ia - y_ib
+  const float* Y;   // n x k (generic-k kernels read coordinates)
+  const void* delta;
+  int64_t ldd;
+  const float* col_scale;
+  int64_t tiles;
+  int64_t plane;
+  float* h;          // k = 2: n scalars sum_j r_ij sign; else n x k sums of r_ij T
+  double* stress;    // FP64 accumulator of sum r^2
+  PairTab tab;
+  unsigned* err;
+};
+
+// ------------------------------------------------------------ point prep ---
+
+template <int K>
+__global__ void k_prep(const float* __restrict__ Y, int64_t n, float2* __restrict__ P,
+                       unsigned* err) {
+  constexpr int NP = K * (K - 1) / 2;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  bool bad = false;
+  if (i < n) {
+    float y[K];
+#pragma unroll
+    for (int c = 0; c < K; ++c) {
+      y[c] = Y[i * K + c];
+      bad |= !isfinite(y[c]);
+    }
+    int p = 0;
+#pragma unroll
+    for (int a = 0; a < K; ++a)
+#pragma unroll
+      for (int b = a + 1; b < K; ++b) P[i * NP + (p++)] = two_diff(y[a], y[b]);
+  }
+  if (__any_sync(FULL_MASK, bad) && (threadIdx.x & 31) == 0) raise_error(err, ERR_NONFINITE);
+}
+
+// ------------------------------------------------------- pair functions ---
+
+// k = 2: residual r = 2^{1-nu}|u_i - u_j| - delta and t = r * sign(u_i - u_j).
+__device__ __forceinline__ void pair2(float2 ui, float2 uj, float c2, float delta, float& r,
+                                      float& t) {
+  const float dh = ui.x - uj.x, dl = ui.y - uj.y;
+  r = fmaf(c2, fabsf(dh + dl), -delta);
+  const float sg = (dh != 0.f) ? dh : dl;  // exact sign of u_i - u_j
+  t = (sg == 0.f) ? 0.f : copysignf(r, sg);
+}
+
+// Generic k: distance and dd/dy_i (= T[2R_c - 2]) with exact rank comparisons.
+template <int K>
+__device__ __forceinline__ float pair_k(const float* yi, const float* yj, const float2* Pi,
+                                        const float2* Pj, const float* w, float (&dw)[K]) {
+  int r2[K];
+#pragma unroll
+  for (int a = 0; a < K; ++a) r2[a] = 2;
+  int p = 0;
+#pragma unroll
+  for (int a = 0; a < K; ++a)
+#pragma unroll
+    for (int b = a + 1; b < K; ++b) {
+      const int c = exact_cmp(Pi[p], Pj[p]);  // sign(z_a - z_b)
+      r2[a] += 1 + c;
+      r2[b] += 1 - c;
+      ++p;
+    }
+  float d = 0.f;
+#pragma unroll
+  for (int a = 0; a < K; ++a) {
+    dw[a] = w[r2[a] - 2];
+    d = fmaf(yi[a] - yj[a], dw[a], d);
+  }
+  return d;
+}
+
+// ------------------------------------------------------------ plain form ---
+
+// One warp per row i.  FWD: S over j > i.  !FWD: h_i over all j != i.
+template <int K, bool FWD>
+__global__ void __launch_bounds__(256) k_full(const IterParams Q) {
+  constexpr int NP = K * (K - 1) / 2;
+  __shared__ float s_w[2 * KMAX - 1];
+  __shared__ double s_red[8];
+  if (threadIdx.x < 2 * KMAX - 1) s_w[threadIdx.x] = Q.tab.w[threadIdx.x];
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const float* D = reinterpret_cast<const float*>(Q.delta);
+  double Sd = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * 8 + warp; i < Q.n; i += (int64_t)gridDim.x * 8) {
+    float yi[K];
+    float2 Pi[NP];
+#pragma unroll
+    for (int c = 0; c < K; ++c) yi[c] = Q.Y[i * K + c];
+#pragma unroll
+    for (int p = 0; p < NP; ++p) Pi[p] = Q.P[i * NP + p];
+    float acc[K];
+#pragma unroll
+    for (int c = 0; c < K; ++c) acc[c] = 0.f;
+    float S = 0.f;
+    int cnt = 0;
+    for (int64_t j = (FWD ? i + 1 : 0) + lane; j < Q.n; j += 32) {
+      const float dl = __ldcs(D + i * Q.ldd + j);
+      if (K == 2) {
+        float r, t;
+        pair2(Pi[0], Q.P[j], Q.tab.c2, dl, r, t);
+        if (FWD) S = fmaf(r, r, S);
+        else if (j != i) acc[0] += t;
+      } else {
+        float yj[K], dw[K];
+        float2 Pj[NP];
+#pragma unroll
+        for (int c = 0; c < K; ++c) yj[c] = Q.Y[j * K + c];
+#pragma unroll
+        for (int p = 0; p < NP; ++p) Pj[p] = Q.P[j * NP + p];
+        const float r = pair_k<K>(yi, yj, Pi, Pj, s_w, dw) - dl;
+        if (FWD) {
+          S = fmaf(r, r, S);
+        } else if (j != i) {
+#pragma unroll
+          for (int c = 0; c < K; ++c) acc[c] = fmaf(r, dw[c], acc[c]);
+        }
+      }
+      if (FWD && ++cnt == 32) {  // flush FP32 partials into FP64 every 32 terms
+        Sd += (double)S;
+        S = 0.f;
+        cnt = 0;
+      }
+    }
+    if (FWD) {
+      Sd += (double)S;
+    } else {
+#pragma unroll
+      for (int c = 0; c < K; ++c) {
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) acc[c] += __shfl_xor_sync(FULL_MASK, acc[c], o);
+      }
+      if (lane == 0) {
+        if (K == 2) Q.h[i] = acc[0];
+        else
+#pragma unroll
+          for (int c = 0; c < K; ++c) Q.h[i * K + c] = acc[c];
+      }
+    }
+  }
+  if (FWD) {
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) Sd += __shfl_xor_sync(FULL_MASK, Sd, o);
+    if (lane == 0) s_red[warp] = Sd;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double s = 0.0;
+      for (int w = 0; w < 8; ++w) s += s_red[w];
+      atomicAdd(Q.stress, s);
+    }
+  }
+}
+
+// ------------------------------------------------------------ fused form ---
+
+// Loads 4 consecutive stored dissimilarities (columns 4*lane .. 4*lane+3 of a
+// tile row) and widens them to float.
+template <int DT>
+__device__ __forceinline__ void load4(const IterParams& Q, int64_t off, float (&d)[4],
+                                      const float (&sc)[4]) {
+  if (DT == GINI_F32) {
+    const float4 v = __ldcs(reinterpret_cast<const float4*>(reinterpret_cast<const float*>(Q.delta) + off));
+    d[0] = v.x; d[1] = v.y; d[2] = v.z; d[3] = v.w;
+  } else if (DT == GINI_BF16 || DT == GINI_BF16X2) {
+    const uint16_t* base = reinterpret_cast<const uint16_t*>(Q.delta);
+    const uint2 h = __ldcs(reinterpret_cast<const uint2*>(base + off));
+    d[0] = bf16_bits_to_float(h.x & 0xffffu);
+    d[1] = __uint_as_float(h.x & 0xffff0000u);
+    d[2] = bf16_bits_to_float(h.y & 0xffffu);
+    d[3] = __uint_as_float(h.y & 0xffff0000u);
+    if (DT == GINI_BF16X2) {
+      const uint2 l = __ldcs(reinterpret_cast<const uint2*>(base + Q.plane + off));
+      d[0] += bf16_bits_to_float(l.x & 0xffffu);
+      d[1] += __uint_as_float(l.x & 0xffff0000u);
+      d[2] += bf16_bits_to_float(l.y & 0xffffu);
+      d[3] += __uint_as_float(l.y & 0xffff0000u);
+    }
+  } else {  // GINI_FP8E4M3
+    const uint32_t q = __ldcs(reinterpret_cast<const unsigned int*>(
+        reinterpret_cast<const uint8_t*>(Q.delta) + off));
+    const __half2_raw lo = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(q & 0xffffu), __NV_E4M3);
+    const __half2_raw hi = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(q >> 16), __NV_E4M3);
+    const float2 a = __half22float2(__half2(lo));
+    const float2 b = __half22float2(__half2(hi));
+    d[0] = a.x * sc[0]; d[1] = a.y * sc[1]; d[2] = b.x * sc[2]; d[3] = b.y * sc[3];
+  }
+}
+
+// Sums a[0..15] over the 32 lanes of a warp by recursive halving; lane l
+// returns the total of entry rev4(l & 15) (bits 0..3 of l reversed).
+__device__ __forceinline__ float reduce16(float (&a)[16], int lane) {
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    const int h = 8 >> s, x = 1 << s;
+    const bool upper = (lane & x) != 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      if (i < h) {
+        const float send = upper ? a[i] : a[i + h];
+        const float keep = upper ? a[i + h] : a[i];
+        a[i] = keep + __shfl_xor_sync(FULL_MASK, send, x);
+      }
+    }
+  }
+  return a[0] + __shfl_xor_sync(FULL_MASK, a[0], 16);
+}
+
+__device__ __forceinline__ int rev4(int l) {
+  return ((l & 1) << 3) | ((l & 2) << 1) | ((l & 4) >> 1) | ((l & 8) >> 3);
+}
+
+__device__ __forceinline__ void block_add_stress(double v, double* dst) {
+  __shared__ double s_red[FUSED_THREADS / 32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(FULL_MASK, v, o);
+  if (lane == 0) s_red[warp] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < FUSED_THREADS / 32; ++w) s += s_red[w];
+    atomicAdd(dst, s);
+  }
+}
+
+// k = 2 fused kernel.  Persistent CTAs walk tiles t = blockIdx.x + q gridDim.x.
+template <int DT, bool GRAD>
+__global__ void __launch_bounds__(FUSED_THREADS) k_fused2(const IterParams Q, int64_t ntiles) {
+  __shared__ float s_col[FUSED_THREADS / 32][TILE];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const float c2 = Q.tab.c2;
+  double Sd = 0.0;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    int I, J;
+    tile_decode(t, Q.tiles, I, J);
+    const int64_t i0 = (int64_t)I * TILE, j0 = (int64_t)J * TILE;
+    float2 uc[4];
+    float sc[4];
+    int64_t gjv[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      gjv[c] = j0 + 4 * lane + c;
+      const int64_t gj = gjv[c] < Q.n ? gjv[c] : Q.n - 1;
+      uc[c] = Q.P[gj];
+      sc[c] = (DT == GINI_FP8E4M3) ? Q.col_scale[gj] : 1.f;
+    }
+    const int rbase = warp * 16;
+    const int64_t gil = i0 + rbase + (lane & 15);
+    const float2 url = Q.P[gil < Q.n ? gil : Q.n - 1];
+    const int64_t tbase = t * (int64_t)(TILE * TILE);
+    float colacc[4] = {0.f, 0.f, 0.f, 0.f};
+    float rowacc[16];
+    float S = 0.f;
+#pragma unroll
+    for (int rr = 0; rr < 16; ++rr) {
+      const int rl = rbase + rr;
+      const int64_t gi = i0 + rl;
+      const float2 ur = make_float2(__shfl_sync(FULL_MASK, url.x, rr),
+                                    __shfl_sync(FULL_MASK, url.y, rr));
+      float dl[4];
+      load4<DT>(Q, tbase + (int64_t)rl * TILE + 4 * lane, dl, sc);
+      float ra = 0.f;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const bool ok = gi < Q.n && gjv[c] < Q.n && (I != J || rl < 4 * lane + c);
+        float r, tt;
+        pair2(ur, uc[c], c2, dl[c], r, tt);
+        r = ok ? r : 0.f;
+        tt = ok ? tt : 0.f;
+        S = fmaf(r, r, S);
+        ra += tt;
+        colacc[c] -= tt;
+      }
+      rowacc[rr] = ra;
+    }
+    Sd += (double)S;
+    if (GRAD) {
+      const float rs = reduce16(rowacc, lane);
+      if (lane < 16) {
+        const int64_t gi = i0 + rbase + rev4(lane);
+        if (gi < Q.n) atomicAdd(Q.h + gi, rs);
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c) s_col[warp][4 * lane + c] = colacc[c];
+      __syncthreads();
+      if (threadIdx.x < TILE) {
+        float s = 0.f;
+#pragma unroll
+        for (int w = 0; w < FUSED_THREADS / 32; ++w) s += s_col[w][threadIdx.x];
+        const int64_t gj = j0 + threadIdx.x;
+        if (gj < Q.n) atomicAdd(Q.h + gj, s);
+      }
+      __syncthreads();
+    }
+  }
+  block_add_stress(Sd, Q.stress);
+}
+
+// Generic k (3..8) fused kernel: the tile's row and column points are staged
+// in shared memory; a lane takes 4 columns of each of its warp's 16 rows.
+template <int K>
+struct FusedKSmem {
+  static constexpr int NP = K * (K - 1) / 2;
+  float2 p[2][TILE][NP];
+  float y[2][TILE][K];
+  float colh[TILE][K];
+};
+
+template <int K, int DT, bool GRAD>
+__global__ void __launch_bounds__(FUSED_THREADS) k_fusedk(const IterParams Q, int64_t ntiles) {
+  constexpr int NP = K * (K - 1) / 2;
+  extern __shared__ __align__(16) unsigned char s_raw[];
+  FusedKSmem<K>& sm = *reinterpret_cast<FusedKSmem<K>*>(s_raw);
+  auto& s_p = sm.p;
+  auto& s_y = sm.y;
+  auto& s_colh = sm.colh;
+  __shared__ float s_w[2 * KMAX - 1];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x < 2 * KMAX - 1) s_w[threadIdx.x] = Q.tab.w[threadIdx.x];
+  for (int e = threadIdx.x; e < TILE * K; e += FUSED_THREADS) (&s_colh[0][0])[e] = 0.f;
+  double Sd = 0.0;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    int I, J;
+    tile_decode(t, Q.tiles, I, J);
+    const int64_t i0 = (int64_t)I * TILE, j0 = (int64_t)J * TILE;
+    __syncthreads();
+    for (int e = threadIdx.x; e < 2 * TILE; e += FUSED_THREADS) {
+      const int side = e / TILE, l = e % TILE;
+      int64_t g = (side ? j0 : i0) + l;
+      g = g < Q.n ? g : Q.n - 1;
+#pragma unroll
+      for (int c = 0; c < K; ++c) s_y[side][l][c] = Q.Y[g * K + c];
+#pragma unroll
+      for (int p = 0; p < NP; ++p) s_p[side][l][p] = Q.P[g * NP + p];
+    }
+    __syncthreads();
+    float sc[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int64_t gj = j0 + 4 * lane + c;
+      sc[c] = (DT == GINI_FP8E4M3) ? Q.col_scale[gj < Q.n ? gj : Q.n - 1] : 1.f;
+    }
+    const int64_t tbase = t * (int64_t)(TILE * TILE);
+    float colacc[4][K];
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+      for (int a = 0; a < K; ++a) colacc[c][a] = 0.f;
+    float S = 0.f;
+    for (int rr = 0; rr < 16; ++rr) {
+      const int rl = warp * 16 + rr;
+      const int64_t gi = i0 + rl;
+      float dl[4];
+      load4<DT>(Q, tbase + (int64_t)rl * TILE + 4 * lane, dl, sc);
+      float racc[K];
+#pragma unroll
+      for (int a = 0; a < K; ++a) racc[a] = 0.f;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int cl = 4 * lane + c;
+        const bool ok = gi < Q.n && j0 + cl < Q.n && (I != J || rl < cl);
+        float dw[K];
+        float r = pair_k<K>(s_y[0][rl], s_y[1][cl], s_p[0][rl], s_p[1][cl], s_w, dw) - dl[c];
+        r = ok ? r : 0.f;
+        S = fmaf(r, r, S);
+#pragma unroll
+        for (int a = 0; a < K; ++a) {
+          const float tt = r * dw[a];
+          racc[a] += tt;
+          colacc[c][a] -= tt;
+        }
+      }
+      if (GRAD) {
+#pragma unroll
+        for (int a = 0; a < K; ++a) {
+#pragma unroll
+          for (int o = 16; o >= 1; o >>= 1) racc[a] += __shfl_xor_sync(FULL_MASK, racc[a], o);
+        }
+        if (lane == 0 && gi < Q.n)
+#pragma unroll
+          for (int a = 0; a < K; ++a) atomicAdd(Q.h + gi * K + a, racc[a]);
+      }
+    }
+    Sd += (double)S;
+    if (GRAD) {
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int a = 0; a < K; ++a) atomicAdd(&s_colh[4 * lane + c][a], colacc[c][a]);
+      __syncthreads();
+      for (int e = threadIdx.x; e < TILE * K; e += FUSED_THREADS) {
+        const int l = e / K, a = e % K;
+        const int64_t gj = j0 + l;
+        const float v = s_colh[l][a];
+        s_colh[l][a] = 0.f;
+        if (gj < Q.n) atomicAdd(Q.h + gj * K + a, v);
+      }
+    }
+  }
+  block_add_stress(Sd, Q.stress);
+}
+
+// ------------------------------------------------------ update, finalize ---
+
+// Y <- Y - scale * h (scale = eta * 2 / sum_delta2; for k = 2 the gradient is
+// c2 * h_i * (1, -1)), then refresh the point pairs and clear h.
+template <int K>
+__global__ void k_update(float* __restrict__ Y, int64_t n, float2* __restrict__ P,
+                         float* __restrict__ h, float scale, float c2, unsigned* err) {
+  constexpr int NP = K * (K - 1) / 2;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  bool bad = false;
+  if (i < n) {
+    float y[K];
+#pragma unroll
+    for (int c = 0; c < K; ++c) y[c] = Y[i * K + c];
+    if (K == 2) {
+      const float g = scale * c2 * h[i];
+      y[0] -= g;
+      y[1] += g;
+      h[i] = 0.f;
+    } else {
+#pragma unroll
+      for (int c = 0; c < K; ++c) {
+        y[c] -= scale * h[i * K + c];
+        h[i * K + c] = 0.f;
+      }
+    }
+    int p = 0;
+#pragma unroll
+    for (int c = 0; c < K; ++c) {
+      Y[i * K + c] = y[c];
+      bad |= !isfinite(y[c]);
+    }
+#pragma unroll
+    for (int a = 0; a < K; ++a)
+#pragma unroll
+      for (int b = a + 1; b < K; ++b) P[i * NP + (p++)] = two_diff(y[a], y[b]);
+  }
+  if (__any_sync(FULL_MASK, bad) && (threadIdx.x & 31) == 0) raise_error(err, ERR_NONFINITE);
+}
+
+__global__ void k_finalize_grad(const float* __restrict__ h, int64_t n, int k, float scale,
+                                float c2, float* __restrict__ grad) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (k == 2) {
+    const float g = scale * c2 * h[i];
+    grad[i * 2] = g;
+    grad[i * 2 + 1] = -g;
+  } else {
+    for (int c = 0; c < k; ++c) grad[i * k + c] = scale * h[i * k + c];
+  }
+}
+
+__global__ void k_finalize_stress(const double* acc, int cnt, double inv_sd2, double* hist,
+                                  double* final_out) {
+  for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+    const double v = acc[t] * inv_sd2;
+    if (hist) hist[t] = v;
+    if (final_out && t == cnt - 1) final_out[0] = v;
+  }
+}
+
+// ---------------------------------------------------------------- host -----
+
+struct IterWs {
+  float2* P;
+  float* h;
+  double* acc;
+  unsigned* err;
+};
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace gini
+
+using namespace gini;
+
+extern "C" void gini_set_cuda_error(cudaError_t e);
+
+// Workspace of the iteration ops: header | nacc doubles | point pairs | h.
+extern "C" size_t gini_iter_ws_bytes(int64_t n, int k, int nacc) {
+  const int np = k * (k - 1) / 2;
+  return WS_HEADER + align256(sizeof(double) * (size_t)nacc) +
+         align256(sizeof(float2) * (size_t)n * np) + align256(sizeof(float) * (size_t)n * k);
+}
+
+static IterWs carve(void* ws, int64_t n, int k, int nacc) {
+  IterWs w;
+  char* p = reinterpret_cast<char*>(ws);
+  w.err = reinterpret_cast<unsigned*>(p);
+  p += WS_HEADER;
+  w.acc = reinterpret_cast<double*>(p);
+  p += align256(sizeof(double) * (size_t)nacc);
+  w.P = reinterpret_cast<float2*>(p);
+  p += align256(sizeof(float2) * (size_t)n * (k * (k - 1) / 2));
+  w.h = reinterpret_cast<float*>(p);
+  return w;
+}
+
+static PairTab make_tab(int k, double nu) {
+  PairTab T{};
+  T.c2 = (float)pow(2.0, 1.0 - nu);
+  const double d = (double)k;
+  for (int idx = 0; idx <= 2 * k - 2; ++idx) {
+    const double R = (idx + 2) / 2.0;
+    T.w[idx] = (float)(0.5 * d * (pow((R - 1.0) / d, nu - 1.0) - pow((d - R) / d, nu - 1.0)));
+  }
+  return T;
+}
+
+static int sm_count() {
+  static int cached = 0;
+  if (!cached) {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+      cached = v;
+    else
+      return 148;
+  }
+  return cached;
+}
+
+static int check_common(int64_t n, int k, double nu, const void* delta, int layout, int dtype,
+                        int64_t ldd, const float* col_scale, double sum_delta2) {
+  if (!delta) return GINI_EINVAL;
+  if (n < 2 || n > ((int64_t)1 << 31) || k < 2 || k > KMAX) return GINI_EINVAL;
+  if (!(nu > 1.0) || !isfinite(nu)) return GINI_EINVAL;
+  if (layout == GINI_LAYOUT_FULL) {
+    if (dtype != GINI_F32 || ldd < n) return GINI_EINVAL;
+  } else if (layout == GINI_LAYOUT_TILED) {
+    if (dtype < GINI_F32 || dtype > GINI_FP8E4M3) return GINI_EINVAL;
+    if (dtype == GINI_FP8E4M3 && !col_scale) return GINI_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(delta) & 15) != 0) return GINI_EINVAL;
+  } else {
+    return GINI_EINVAL;
+  }
+  if (!(sum_delta2 > 0.0) || !isfinite(sum_delta2)) return GINI_EDEGENERATE;
+  return GINI_OK;
+}
+
+template <int K>
+static void launch_prep(const float* Y, int64_t n, float2* P, unsigned* err, cudaStream_t s) {
+  gini_count_launch(1);
+  k_prep<K><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(Y, n, P, err);
+}
+
+static void prep(int k, const float* Y, int64_t n, float2* P, unsigned* err, cudaStream_t s) {
+  switch (k) {
+    case 2: launch_prep<2>(Y, n, P, err, s); break;
+    case 3: launch_prep<3>(Y, n, P, err, s); break;
+    case 4: launch_prep<4>(Y, n, P, err, s); break;
+    case 5: launch_prep<5>(Y, n, P, err, s); break;
+    case 6: launch_prep<6>(Y, n, P, err, s); break;
+    case 7: launch_prep<7>(Y, n, P, err, s); break;
+    default: launch_prep<8>(Y, n, P, err, s); break;
+  }
+}
+
+template <int K>
+static void launch_update(float* Y, int64_t n, float2* P, float* h, float scale, float c2,
+                          unsigned* err, cudaStream_t s) {
+  gini_count_launch(1);
+  k_update<K><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(Y, n, P, h, scale, c2, err);
+}
+
+static void update(int k, float* Y, int64_t n, float2* P, float* h, float scale, float c2,
+                   unsigned* err, cudaStream_t s) {
+  switch (k) {
+    case 2: launch_update<2>(Y, n, P, h, scale, c2, err, s); break;
+    case 3: launch_update<3>(Y, n, P, h, scale, c2, err, s); break;
+    case 4: launch_update<4>(Y, n, P, h, scale, c2, err, s); break;
+    case 5: launch_update<5>(Y, n, P, h, scale, c2, err, s); break;
+    case 6: launch_update<6>(Y, n, P, h, scale, c2, err, s); break;
+    case 7: launch_update<7>(Y, n, P, h, scale, c2, err, s); break;
+    default: launch_update<8>(Y, n, P, h, scale, c2, err, s); break;
+  }
+}
+
+template <int K, bool FWD>
+static void launch_full(const IterParams& Q, cudaStream_t s) {
+  const int64_t blocks = (Q.n + 7) / 8;
+  const unsigned g = (unsigned)(blocks < 65535 * 8 ? blocks : 65535 * 8);
+  gini_count_launch(1);
+  k_full<K, FWD><<<g, 256, 0, s>>>(Q);
+}
+
+template <bool FWD>
+static void full_k(int k, const IterParams& Q, cudaStream_t s) {
+  switch (k) {
+    case 2: launch_full<2, FWD>(Q, s); break;
+    case 3: launch_full<3, FWD>(Q, s); break;
+    case 4: launch_full<4, FWD>(Q, s); break;
+    case 5: launch_full<5, FWD>(Q, s); break;
+    case 6: launch_full<6, FWD>(Q, s); break;
+    case 7: launch_full<7, FWD>(Q, s); break;
+    default: launch_full<8, FWD>(Q, s); break;
+  }
+}
+
+template <int K, int DT, bool GRAD>
+static void launch_fusedk(unsigned g, const IterParams& Q, int64_t ntiles, cudaStream_t s) {
+  const size_t smem = sizeof(FusedKSmem<K>);
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(k_fusedk<K, DT, GRAD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+  gini_count_launch(1);
+  k_fusedk<K, DT, GRAD><<<g, FUSED_THREADS, smem, s>>>(Q, ntiles);
+}
+
+template <int DT, bool GRAD>
+static void launch_fused_dt(int k, const IterParams& Q, cudaStream_t s) {
+  const int64_t ntiles = Q.tiles * (Q.tiles + 1) / 2;
+  const int64_t cap = (int64_t)sm_count() * 4;
+  const unsigned g = (unsigned)(ntiles < cap ? ntiles : cap);
+  switch (k) {
+    case 2:
+      gini_count_launch(1);
+      k_fused2<DT, GRAD><<<g, FUSED_THREADS, 0, s>>>(Q, ntiles);
+      break;
+    case 3: launch_fusedk<3, DT, GRAD>(g, Q, ntiles, s); break;
+    case 4: launch_fusedk<4, DT, GRAD>(g, Q, ntiles, s); break;
+    case 5: launch_fusedk<5, DT, GRAD>(g, Q, ntiles, s); break;
+    case 6: launch_fusedk<6, DT, GRAD>(g, Q, ntiles, s); break;
+    case 7: launch_fusedk<7, DT, GRAD>(g, Q, ntiles, s); break;
+    default: launch_fusedk<8, DT, GRAD>(g, Q, ntiles, s); break;
+  }
+}
+
+template <bool GRAD>
+static void launch_fused(int k, int dtype, const IterParams& Q, cudaStream_t s) {
+  switch (dtype) {
+    case GINI_F32: launch_fused_dt<GINI_F32, GRAD>(k, Q, s); break;
+    case GINI_BF16: launch_fused_dt<GINI_BF16, GRAD>(k, Q, s); break;
+    case GINI_BF16X2: launch_fused_dt<GINI_BF16X2, GRAD>(k, Q, s); break;
+    default: launch_fused_dt<GINI_FP8E4M3, GRAD>(k, Q, s); break;
+  }
+}
+
+// One pass: stress into *acc (and h if grad).  dtype_eff lets a BF16X2 matrix
+// be read through its hi plane only.
+static void one_pass(int k, int layout, int dtype_eff, bool grad, const IterParams& Q,
+                     cudaStream_t s) {
+  if (layout == GINI_LAYOUT_FULL) {
+    full_k<true>(k, Q, s);
+    if (grad) full_k<false>(k, Q, s);
+  } else if (grad) {
+    launch_fused<true>(k, dtype_eff, Q, s);
+  } else {
+    launch_fused<false>(k, dtype_eff, Q, s);
+  }
+}
+
+static IterParams make_params(int64_t n, int k, double nu, const float* Y, const void* delta,
+                              int64_t ldd, const float* col_scale, const IterWs& w) {
+  IterParams Q{};
+  Q.n = n;
+  Q.P = w.P;
+  Q.Y = Y;
+  Q.delta = delta;
+  Q.ldd = ldd;
+  Q.col_scale = col_scale;
+  Q.tiles = tiles_1d(n);
+  Q.plane = gini_tiled_elems(n);
+  Q.h = w.h;
+  Q.stress = w.acc;
+  Q.tab = make_tab(k, nu);
+  Q.err = w.err;
+  return Q;
+}
+
+extern "C" int gini_stress_grad(const float* Y_dev, int64_t n, int k, double nu,
+                                const void* delta_dev, int layout, int dtype, int64_t ldd,
+                                const float* col_scale_dev, double sum_delta2, double* stress_dev,
+                                float* grad_dev, void* ws, size_t ws_bytes, void* stream) {
+  if (!Y_dev || !stress_dev || !ws) return GINI_EINVAL;
+  int st = check_common(n, k, nu, delta_dev, layout, dtype, ldd, col_scale_dev, sum_delta2);
+  if (st != GINI_OK) return st;
+  if (ws_bytes < gini_workspace_size(GINI_OP_STRESS, n, 0, k, 0)) return GINI_ENOMEM;
+  cudaStream_t s = (cudaStream_t)stream;
+  IterWs w = carve(ws, n, k, 1);
+  IterParams Q = make_params(n, k, nu, Y_dev, delta_dev, ldd, col_scale_dev, w);
+  cudaError_t e = cudaMemsetAsync(w.acc, 0, sizeof(double), s);
+  if (e == cudaSuccess && grad_dev) e = cudaMemsetAsync(w.h, 0, sizeof(float) * n * k, s);
+  if (e != cudaSuccess) { gini_set_cuda_error(e); return GINI_ECUDA; }
+  prep(k, Y_dev, n, w.P, w.err, s);
+  one_pass(k, layout, dtype, grad_dev != nullptr, Q, s);
+  gini_count_launch(grad_dev ? 2 : 1);
+  k_finalize_stress<<<1, 32, 0, s>>>(w.acc, 1, 1.0 / sum_delta2, nullptr, stress_dev);
+  if (grad_dev)
+    k_finalize_grad<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
+        w.h, n, k, (float)(2.0 / sum_delta2), Q.tab.c2, grad_dev);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) { gini_set_cuda_error(e); return GINI_ECUDA; }
+  return GINI_OK;
+}
+
+extern "C" int gini_mds_fit(const gini_fit_args* a, void* ws, size_t ws_bytes, void* stream) {
+  if (!a || !ws || !a->Y_dev) return GINI_EINVAL;
+  int st = check_common(a->n, a->k, a->nu, a->delta_dev, a->layout, a->dtype, a->ldd,
+                        a->col_scale_dev, a->sum_delta2);
+  if (st != GINI_OK) return st;
+  if (a->iters < 0 || !(a->eta > 0.0) || !isfinite(a->eta) || a->polish_iters < 0)
+    return GINI_EINVAL;
+  if (ws_bytes < gini_workspace_size(GINI_OP_FIT, a->n, 0, a->k, a->iters)) return GINI_ENOMEM;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t n = a->n;
+  const int k = a->k;
+  const int T = a->iters;
+  IterWs w = carve(ws, n, k, T + 1);
+  IterParams Q = make_params(n, k, a->nu, a->Y_dev, a->delta_dev, a->ldd, a->col_scale_dev, w);
+  cudaError_t e = cudaMemsetAsync(w.acc, 0, sizeof(double) * (size_t)(T + 1), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(w.h, 0, sizeof(float) * n * k, s);
+  if (e != cudaSuccess) { gini_set_cuda_error(e); return GINI_ECUDA; }
+  prep(k, a->Y_dev, n, w.P, w.err, s);
+  const float scale = (float)(a->eta * 2.0 / a->sum_delta2);
+  const int polish_from = T - (a->polish_iters < T ? a->polish_iters : T);
+  for (int t = 0; t < T; ++t) {
+    int dt = a->dtype;
+    if (dt == GINI_BF16X2 && a->layout == GINI_LAYOUT_TILED && t < polish_from) dt = GINI_BF16;
+    Q.stress = w.acc + t;
+    one_pass(k, a->layout, dt, true, Q, s);
+    update(k, a->Y_dev, n, w.P, w.h, scale, Q.tab.c2, w.err, s);
+  }
+  Q.stress = w.acc + T;
+  one_pass(k, a->layout, a->dtype, false, Q, s);
+  gini_count_launch(1);
+  k_finalize_stress<<<1, 256, 0, s>>>(w.acc, T + 1, 1.0 / a->sum_delta2, a->history_dev,
+                                      a->final_stress_dev);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) { gini_set_cuda_error(e); return GINI_ECUDA; }
+  return GINI_OK;
+}

@@ -1,0 +1,149 @@
+"""gini_dist (Delta build) on the GPU against the FP64 oracle.
+
+Tolerances (relative to each entry, with a floor of 1e-6 x the largest entry
+for near-zero dissimilarities): FP32 1e-5; BF16 2e-3 (round-to-nearest bound
+2^-9 plus the FP32 error); BF16 hi+lo 1e-5 (bound 2^-18); FP8 reported only.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import gini_oracle as orc
+from paper_2605_25124_gb300 import workloads as wl
+from util import rel_err, untile
+
+pytestmark = pytest.mark.gpu
+
+
+def _gpu_full(G, X, nus):
+    mats, sd2 = G.gini_dist(torch.from_numpy(X).cuda(), nus, layout="full")
+    return [m.data.cpu().numpy().astype(np.float64) for m in mats], sd2.cpu().numpy()
+
+
+def _check_full(got, ref, tol=1e-5):
+    floor = 1e-6 * np.abs(ref).max()
+    assert rel_err(got, ref, floor) <= tol
+    np.testing.assert_array_equal(got, got.T)
+    assert np.all(np.diag(got) == 0)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 7, 10, 16, 33, 50, 64, 100, 129, 300, 784, 1024])
+def test_delta_full_f32_all_vector_lengths(G, p):
+    n = 41 if p < 300 else 23
+    X = wl.gaussian_outliers(n, p, seed=100 + p)
+    nus = [1.5, 2.0, 3.0]
+    ref, sref = orc.delta(X, nus)
+    got, sd2 = _gpu_full(G, X, nus)
+    for q in range(3):
+        _check_full(got[q], ref[q])
+        assert sd2[q] == pytest.approx(sref[q], rel=1e-5)
+
+
+@pytest.mark.parametrize("nu", [2.0, 1.1, 4.5])
+def test_delta_single_nu_paths(G, nu):
+    # nu = 2 alone takes the positional-weight path; other nu the tie-run path.
+    X = wl.image_like(30, seed=7)
+    ref, sref = orc.delta(X, [nu])
+    got, sd2 = _gpu_full(G, X, [nu])
+    _check_full(got[0], ref[0])
+    assert sd2[0] == pytest.approx(sref[0], rel=1e-5)
+
+
+def test_delta_ties_integer_and_image_data(G):
+    for X in (wl.integer_valued(60, 50, seed=8), wl.image_like(40, seed=9),
+              wl.uci_like_batch(4, seed=10)[3][:50]):
+        nus = [1.5, 2.0, 3.0]
+        ref, _ = orc.delta(X, nus)
+        got, _ = _gpu_full(G, X, nus)
+        for q in range(3):
+            _check_full(got[q], ref[q])
+
+
+def test_delta_affine_path_equals_table_path(G):
+    X = wl.image_like(50, seed=11)
+    a, _ = _gpu_full(G, X, [2.0])
+    b, _ = _gpu_full(G, X, [2.0, 2.0])
+    assert rel_err(a[0], b[0], 1e-6 * np.abs(a[0]).max()) <= 2e-6
+
+
+@pytest.mark.parametrize("dtype,tol", [("f32", 1e-5), ("bf16", 2e-3), ("bf16x2", 1e-5)])
+def test_delta_tiled_layouts(G, dtype, tol):
+    n = 300  # 3 tiles per edge, ragged tail of 44
+    X = wl.gaussian_mixture(n, 20, seed=12)
+    nus = [1.5, 2.0]
+    ref, sref = orc.delta(X, nus)
+    mats, sd2 = G.gini_dist(torch.from_numpy(X).cuda(), nus, layout="tiled", dtype=dtype)
+    planes = 2 if dtype == "bf16x2" else 1
+    for q in range(2):
+        flat = mats[q].data.float().cpu().numpy()
+        got = untile(flat, n, planes)
+        iu = np.triu_indices(n, 1)
+        floor = 1e-6 * np.abs(ref[q]).max()
+        assert rel_err(got[iu], ref[q][iu], floor) <= tol
+        assert sd2.cpu().numpy()[q] == pytest.approx(sref[q], rel=1e-5)
+
+
+def test_pack_from_full(G):
+    n = 260
+    X = wl.gaussian_outliers(n, 9, seed=13)
+    ref, _ = orc.delta(X, [1.8])
+    mats, _ = G.gini_dist(torch.from_numpy(X).cuda(), [1.8], layout="full")
+    iu = np.triu_indices(n, 1)
+    floor = 1e-6 * np.abs(ref[0]).max()
+    for dtype, tol in (("f32", 1e-5), ("bf16", 2e-3), ("bf16x2", 1e-5)):
+        P = G.gini_pack(mats[0], dtype)
+        got = untile(P.data.float().cpu().numpy(), n, 2 if dtype == "bf16x2" else 1)
+        assert rel_err(got[iu], ref[0][iu], floor) <= tol, dtype
+    P = G.gini_pack(mats[0], "fp8")
+    q = P.data.cpu().numpy().view(np.uint8)
+    sc = P.col_scale.cpu().numpy()
+    # decode e4m3 on the host (sign, 4-bit exponent with bias 7, 3-bit mantissa)
+    s = np.where(q & 0x80, -1.0, 1.0)
+    e = (q >> 3) & 0xF
+    mant = (q & 7).astype(np.float64)
+    val = s * np.where(e == 0, mant / 8 * 2.0 ** -6, (1 + mant / 8) * 2.0 ** (e.astype(np.float64) - 7))
+    T = -(-n // 128)
+    full = untile(val, n) * sc[None, :]
+    err = np.abs(full[iu] - ref[0][iu])
+    # normal e4m3: half an ulp of a 3-bit mantissa (2^-4 relative); subnormal: 2^-10 absolute
+    bound = 2.0 ** -4 * np.abs(ref[0][iu]) + 2.0 ** -10 * sc[iu[1]]
+    assert np.all(err <= bound + 1e-6)
+    colmax = np.max(np.triu(ref[0], 1), axis=0)
+    np.testing.assert_allclose(sc[1:], np.where(colmax[1:] > 0, colmax[1:] / 448, 1), rtol=1e-5)
+    assert T >= 3
+
+
+def test_delta_full_size_image_workload_sampled(G):
+    """n = 2000, p = 784, nu in {1.5, 2, 3}: the whole matrix on the GPU,
+    300 sampled pairs (and one full row) from the oracle."""
+    w = wl.WORKLOADS["image-n2000-p784"]
+    X = wl.make_X("image-n2000-p784")
+    mats, sd2 = G.gini_dist(torch.from_numpy(X).cuda(), w["nu"], layout="full")
+    rng = np.random.default_rng(14)
+    I = rng.integers(0, w["n"], 300)
+    J = rng.integers(0, w["n"], 300)
+    I = np.concatenate([I, np.full(w["n"], 1234)])
+    J = np.concatenate([J, np.arange(w["n"])])
+    ref = orc.delta_pairs(X, w["nu"], I, J)
+    for q in range(3):
+        got = mats[q].data[torch.from_numpy(I).cuda(), torch.from_numpy(J).cuda()].cpu().numpy()
+        assert rel_err(got, ref[:, q], 1e-6 * np.abs(ref[:, q]).max()) <= 1e-5
+    # sum of squares by symmetry of the stored square
+    for q in range(3):
+        d = mats[q].data.double()
+        assert sd2[q].item() == pytest.approx(0.5 * float((d * d).sum()), rel=1e-9)
+
+
+def test_delta_nonfinite_reported(G):
+    from paper_2605_25124_gb300._lib import GiniError
+    X = wl.gaussian_outliers(20, 6, seed=15)
+    X[3, 2] = np.inf
+    with pytest.raises(GiniError, match="ENONFINITE"):
+        G.gini_dist(torch.from_numpy(X).cuda(), [2.0])
+
+
+def test_delta_two_points_worked_example(G):
+    X = np.array([[10, 1200], [10, 12]], dtype=np.float32)
+    mats, sd2 = G.gini_dist(torch.from_numpy(X).cuda(), [2.0, 1.5, 3.0])
+    for q, nu in enumerate([2.0, 1.5, 3.0]):
+        assert mats[q].data[0, 1].item() == pytest.approx(1188 * 2.0 ** (1 - nu), rel=1e-6)

@@ -1,0 +1,156 @@
+"""gini_stress_grad (plain FULL form and fused TILED form) and the GiniStress
+autograd op on the GPU against the FP64 oracle.
+
+Tolerances: stress relative 1e-5; gradient max-abs error <= 1e-5 x max |grad|
+(an FP32 sum of n terms with cancellation is only accurate relative to the
+scale of its terms); finite differences relative 1e-3.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import gini_oracle as orc
+from paper_2605_25124_gb300 import workloads as wl
+from util import host_col_scale, quantize, tile_pack
+
+pytestmark = pytest.mark.gpu
+
+
+def _dis(G, full_ref, n, dtype, sd2):
+    """Upload a host matrix as the library's Dissimilarity in layout/dtype."""
+    if dtype == "full":
+        t = torch.from_numpy(np.asarray(full_ref, dtype=np.float32)).cuda()
+        return G.Dissimilarity(t, n, "full", "f32", sd2)
+    sc = host_col_scale(full_ref) if dtype == "fp8" else None
+    flat = tile_pack(full_ref, n, dtype, sc)
+    t = torch.from_numpy(flat).cuda()
+    return G.Dissimilarity(t, n, "tiled", dtype, sd2,
+                           torch.from_numpy(sc).cuda() if sc is not None else None)
+
+
+def _ref_delta(n, p, nu, seed):
+    X = wl.gaussian_outliers(n, p, seed=seed)
+    D, s = orc.delta(X, [nu])
+    return X, D[0], float(s[0])
+
+
+@pytest.mark.parametrize("dtype", ["full", "f32", "bf16", "bf16x2", "fp8"])
+@pytest.mark.parametrize("k,nu", [(2, 2.0), (2, 1.5), (3, 3.0), (4, 1.3), (8, 2.0)])
+def test_stress_grad_parity(G, dtype, k, nu):
+    n = 300  # 3 tiles per edge, ragged tail
+    X, D, sd2 = _ref_delta(n, 8, nu, seed=200 + k)
+    sc = host_col_scale(D) if dtype == "fp8" else None
+    Dq = quantize(D, "f32" if dtype == "full" else dtype, sc)
+    Dq = np.triu(Dq, 1) + np.triu(Dq, 1).T
+    Y = wl.y_init(n, k, seed=201 + k, sd=1.0)
+    Sref, gref = orc.stress_grad(Y.astype(np.float64), nu, Dq, sd2)
+    S, g = G.gini_stress_grad(torch.from_numpy(Y).cuda(), nu, _dis(G, D, n, dtype, sd2))
+    assert float(S) == pytest.approx(Sref, rel=1e-5)
+    assert np.max(np.abs(g.cpu().numpy() - gref)) <= 1e-5 * np.abs(gref).max()
+    S2, g2 = G.gini_stress_grad(torch.from_numpy(Y).cuda(), nu, _dis(G, D, n, dtype, sd2),
+                                grad=False)
+    assert g2 is None and float(S2) == pytest.approx(Sref, rel=1e-5)
+
+
+@pytest.mark.parametrize("k,nu", [(2, 2.0), (3, 1.6)])
+def test_planted_embedding_zero_stress(G, k, nu):
+    n = 200
+    Ys = wl.y_init(n, k, seed=210, sd=1.0)
+    I, J = np.triu_indices(n, 1)
+    d = orc.embed_dist_pairs(Ys.astype(np.float64), nu, I, J)
+    D = np.zeros((n, n)); D[I, J] = d; D[J, I] = d
+    sd2 = float(np.sum(d ** 2))
+    for dtype in ("full", "f32"):
+        S, g = G.gini_stress_grad(torch.from_numpy(Ys).cuda(), nu, _dis(G, D, n, dtype, sd2))
+        Yp = Ys + 0.05 * wl.y_init(n, k, seed=211, sd=1.0)
+        Sp, gp = G.gini_stress_grad(torch.from_numpy(Yp).cuda(), nu, _dis(G, D, n, dtype, sd2))
+        assert float(S) < 1e-11 and float(Sp) > 1e-5
+        assert g.abs().max().item() < 1e-4 * gp.abs().max().item()
+
+
+@pytest.mark.parametrize("k", [2, 3])
+def test_gradient_against_central_differences(G, k):
+    # Differences of the stress are taken through the plain form, whose forward
+    # pass rounds each r^2 once and sums in FP64, so unchanged pairs cancel
+    # exactly; the fused gradient must match the plain one.
+    n, nu = 64, 1.8
+    X, D, sd2 = _ref_delta(n, 6, nu, seed=220 + k)
+    Dd = _dis(G, D, n, "full", sd2)
+    Y = wl.y_init(n, k, seed=221, sd=1.0)
+    _, g = G.gini_stress_grad(torch.from_numpy(Y).cuda(), nu, Dd)
+    _, gt = G.gini_stress_grad(torch.from_numpy(Y).cuda(), nu, _dis(G, D, n, "f32", sd2))
+    assert (g - gt).abs().max().item() <= 1e-5 * g.abs().max().item()
+    g = g.cpu().numpy()
+    rng = np.random.default_rng(222)
+    pairs = [(a, b) for a in range(k) for b in range(a + 1, k)]
+    for _ in range(24):
+        i, c = int(rng.integers(n)), int(rng.integers(k))
+        # distance to the nearest kink along y_ic: a tie of z_a and z_b for a
+        # pair (a, b) containing c moves when y_ic moves
+        gap = np.inf
+        for (a, b) in pairs:
+            if c in (a, b):
+                v = (Y[:, a].astype(np.float64) - Y[:, b])
+                dv = np.abs(v[i] - np.delete(v, i))
+                gap = min(gap, dv.min())
+        h = float(min(1e-3, 0.3 * gap))
+        Yp, Ym = Y.copy(), Y.copy()
+        Yp[i, c] += np.float32(h)
+        Ym[i, c] -= np.float32(h)
+        hp, hm = float(Yp[i, c]) - float(Y[i, c]), float(Y[i, c]) - float(Ym[i, c])
+        Sp, _ = G.gini_stress_grad(torch.from_numpy(Yp).cuda(), nu, Dd, grad=False)
+        Sm, _ = G.gini_stress_grad(torch.from_numpy(Ym).cuda(), nu, Dd, grad=False)
+        fd = (float(Sp) - float(Sm)) / (hp + hm)
+        assert g[i, c] == pytest.approx(fd, rel=1e-3, abs=1e-3 * np.abs(g).max())
+
+
+@pytest.mark.parametrize("k", [2, 3])
+def test_adjoint_at_mixture_scale_sampled_rows(G, k):
+    """n = 5000, p = 50 Gaussian mixture with heavy-tailed rows: the GPU
+    gradient (plain and fused) against oracle gradient rows."""
+    n, p, nu = 5000, 50, 2.0
+    X = wl.gaussian_mixture(n, p, seed=wl.SEED_BASE + 3)
+    Y = wl.y_init(n, k, seed=230 + k, sd=1.0)
+    mats, _ = G.gini_dist(torch.from_numpy(X).cuda(), [nu], layout="full")
+    Dg = G.Dissimilarity(mats[0].data, n, "full", "f32", 1.0)  # sum_delta2 = 1 on both sides
+    Yd = torch.from_numpy(Y).cuda()
+    _, g_full = G.gini_stress_grad(Yd, nu, Dg)
+    Dt = G.gini_pack(Dg, "f32")
+    _, g_tiled = G.gini_stress_grad(Yd, nu, Dt)
+    rows = np.random.default_rng(231).choice(n, 12, replace=False)
+    I = np.repeat(rows, n)
+    J = np.tile(np.arange(n), len(rows))
+    Drows = orc.delta_pairs(X, [nu], I, J)[:, 0].reshape(len(rows), n)
+    gref = orc.grad_rows(Y.astype(np.float64), nu, Drows, rows, 1.0)
+    scale = np.abs(gref).max()
+    for g in (g_full, g_tiled):
+        assert np.max(np.abs(g.cpu().numpy()[rows] - gref)) <= 1e-5 * scale
+    assert (g_full - g_tiled).abs().max().item() <= 1e-5 * g_full.abs().max().item()
+
+
+def test_autograd_function(G):
+    n, k, nu = 150, 2, 2.0
+    X, D, sd2 = _ref_delta(n, 5, nu, seed=240)
+    Y = wl.y_init(n, k, seed=241, sd=1.0)
+    Dd = _dis(G, D, n, "bf16x2", sd2)
+    Yt = torch.from_numpy(Y).cuda().requires_grad_(True)
+    S = G.gini_stress(Yt, nu, Dd)
+    (3.0 * S).backward()
+    Sref, gref = orc.stress_grad(Y.astype(np.float64), nu,
+                                 np.triu(quantize(D, "bf16x2"), 1) + np.triu(quantize(D, "bf16x2"), 1).T,
+                                 sd2)
+    assert float(S) == pytest.approx(Sref, rel=1e-5)
+    assert np.max(np.abs(Yt.grad.cpu().numpy() - 3.0 * gref)) <= 1e-5 * 3.0 * np.abs(gref).max()
+    with torch.no_grad():
+        S0 = G.gini_stress(torch.from_numpy(Y).cuda(), nu, Dd)
+    assert float(S0) == pytest.approx(Sref, rel=1e-5)
+
+
+def test_nonfinite_embedding_reported(G):
+    from paper_2605_25124_gb300._lib import GiniError
+    n = 40
+    _, D, sd2 = _ref_delta(n, 4, 2.0, seed=250)
+    Y = wl.y_init(n, 2, seed=251)
+    Y[5, 1] = np.nan
+    with pytest.raises(GiniError, match="ENONFINITE"):
+        G.gini_stress_grad(torch.from_numpy(Y).cuda(), 2.0, _dis(G, D, n, "f32", sd2))
