@@ -37,6 +37,10 @@ sys.path.insert(0, ROOT)
 METRIC = "Gini-MDS iters/s at n=20k,k=2 and Δ-build TFLOP/s, chosen vs plain FP32 form"
 WORKLOAD = "image-n20000-p784"
 POLISH = 40
+# Delta storage forms of the fused iteration: (dtype, iterations reading the
+# lo plane as a fraction of T; None = every iteration)
+FORMS = {"bf16x2": ("bf16x2", None), "f32": ("f32", None), "bf16-polish": ("bf16x2", 0.2),
+         "bf16": ("bf16", None)}
 
 
 def _args():
@@ -48,6 +52,9 @@ def _args():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-form comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end run")
+    ap.add_argument("--form", default="bf16x2", choices=list(FORMS),
+                    help="storage of Delta in the timed fits")
     return ap.parse_args()
 
 
@@ -181,16 +188,19 @@ def run_ours(args, rank, local, world):
     ws = G.workspace(dev)
     Yout = torch.empty_like(Y0)
 
+    f_dtype, f_polish = FORMS[args.form]
+    polish = T if f_polish is None else int(round(f_polish * T))
+
     def step(ev=None):
         if ev is not None:
             ev[0].record(stream)
-        mats, _ = G.gini_dist(X, [nu], layout="tiled", dtype="bf16x2", ws=ws,
+        mats, _ = G.gini_dist(X, [nu], layout="tiled", dtype=f_dtype, ws=ws,
                               check_errors=False)
         if ev is not None:
             ev[1].record(stream)
         D = mats[0]
         eta = G.default_step(n, k, nu, D.sum_delta2, 1.0)
-        Y, _, final = G.gini_mds_fit(Y0, nu, D, eta, T, polish_iters=POLISH, history=False,
+        Y, _, final = G.gini_mds_fit(Y0, nu, D, eta, T, polish_iters=polish, history=False,
                                      ws=ws, check_errors=False, out=Yout)
         if ev is not None:
             ev[2].record(stream)
@@ -239,11 +249,13 @@ def run_ours(args, rank, local, world):
     achieved_ops = P * ops_per_pair / b_s
     traffic = _profile_traffic()
 
-    # iteration phase: BF16 hi plane 2 bytes per stored element (hi+lo = 4 in the
-    # polish iterations); algorithmic bytes = P pairs x bytes per pair.
+    # iteration phase: algorithmic bytes = P pairs x stored bytes per pair
+    # (BF16 hi 2, hi + lo 4, F32 4), averaged over the schedule.
     it_s = statistics.mean(iter_ms) / 1e3 / (T + 1)
-    plane = G.tiled_elems(n)
-    bytes_iter = P * (2 * (T - POLISH) + 4 * POLISH) / T
+    per_pair = {"f32": 4.0, "bf16": 2.0, "bf16x2": 4.0}[f_dtype]
+    if f_dtype == "bf16x2":
+        per_pair = (2.0 * (T - polish) + 4.0 * polish) / T
+    bytes_iter = P * per_pair
     hbm_peak, peak_src = _peaks()
     iter_gbs = bytes_iter / it_s / 1e9
 
@@ -254,8 +266,10 @@ def run_ours(args, rank, local, world):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded image-like 28x28 blobs + noise, clipped; MNIST not available)",
         "config": {"workload": args.workload, "n": n, "p": p, "k": k, "nu": nu, "iters": T,
-                   "delta_storage": "tiled bf16 hi+lo (hi plane for the first "
-                                    f"{T - POLISH} iterations)",
+                   "form": args.form,
+                   "delta_storage": f"tiled upper triangle {f_dtype}"
+                                    + (f", lo plane in the last {polish} iterations"
+                                       if f_dtype == "bf16x2" else ""),
                    "l2": "flushed between steps (256 MB write)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "roofline": {"kernel": "k_dist (Delta build: pair sort + midrank weights)",
@@ -280,14 +294,18 @@ def run_ours(args, rank, local, world):
     }
 
     if not args.no_plain and rank == 0:
-        out["plain_fp32"] = _plain(G, X, Y0, n, k, nu, T, stream, final_stress)
-    out["e2e"] = _e2e(G, X_host, Y0_host, n, p, k, nu, T, args, world)
+        out["plain_fp32"], out["variants"] = _plain_and_variants(G, X, Y0, n, k, nu, T, stream,
+                                                                 final_stress, P)
+    if not args.no_e2e:
+        out["e2e"] = _e2e(G, X_host, Y0_host, n, p, k, nu, T, args, world)
     if rank == 0 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(args.workload, budget_s=12.0)
     return out
 
 
-def _plain(G, X, Y0, n, k, nu, T, stream, chosen_final):
+def _plain_and_variants(G, X, Y0, n, k, nu, T, stream, chosen_final, P):
+    """The plain FP32 form (full-square Delta, separate forward and adjoint
+    kernels), then every tiled form's iteration phase on the same Delta."""
     import torch
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
     torch.cuda.synchronize()
@@ -302,14 +320,36 @@ def _plain(G, X, Y0, n, k, nu, T, stream, chosen_final):
     b = ev[0].elapsed_time(ev[1])
     it = ev[1].elapsed_time(ev[2]) / (T + 1)
     f = float(final)
+    plain = {"form": "full-square FP32 Delta, separate forward and adjoint kernels",
+             "delta_build_ms": round(b, 3), "iter_ms": round(it, 5),
+             "iters_per_s_iteration_phase": round(1e3 / it, 1),
+             "iters_per_s_whole_fit": round(T / ((b + it * (T + 1)) / 1e3), 3),
+             "final_stress": f,
+             "chosen_vs_plain_final_stress_rel_diff": abs(chosen_final - f) / f,
+             "equal_final_stress_1e-4": abs(chosen_final - f) / f <= 1e-4}
+    variants = {}
+    for name, (dt, pol) in FORMS.items():
+        Dv = G.gini_pack(D, dt)
+        polish = T if pol is None else int(round(pol * T))
+        G.gini_mds_fit(Y0, nu, Dv, eta, 5, polish_iters=5, history=False, check_errors=False)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        _, _, fv = G.gini_mds_fit(Y0, nu, Dv, eta, T, polish_iters=polish, history=False,
+                                  check_errors=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        itv = e0.elapsed_time(e1) / (T + 1)
+        bpp = {"f32": 4.0, "bf16": 2.0, "bf16x2": (2.0 * (T - polish) + 4.0 * polish) / T}[dt]
+        variants[name] = {"iter_ms": round(itv, 5), "iters_per_s": round(1e3 / itv, 1),
+                          "achieved_gbs": round(P * bpp / (itv / 1e3) / 1e9, 1),
+                          "final_stress": float(fv),
+                          "final_stress_rel_diff_vs_plain": abs(float(fv) - f) / f,
+                          "speedup_vs_plain": round(it / itv, 3)}
+        del Dv
     del mats, D
     torch.cuda.empty_cache()
-    return {"form": "full-square FP32 Delta, separate forward and adjoint kernels",
-            "delta_build_ms": round(b, 3), "iter_ms": round(it, 5),
-            "iters_per_s_iteration_phase": round(1e3 / it, 1),
-            "iters_per_s_whole_fit": round(T / ((b + it * (T + 1)) / 1e3), 3),
-            "final_stress": f,
-            "chosen_vs_plain_final_stress_rel_diff": abs(chosen_final - f) / f}
+    return plain, variants
 
 
 def _e2e(G, X_host, Y0_host, n, p, k, nu, T, args, world):

@@ -23,6 +23,7 @@
 #include <math.h>
 
 #include "common.cuh"
+#include "pipe.cuh"
 
 namespace gini {
 
@@ -81,7 +82,9 @@ __device__ __forceinline__ void pair2(float2 ui, float2 uj, float c2, float delt
   const float dh = ui.x - uj.x, dl = ui.y - uj.y;
   r = fmaf(c2, fabsf(dh + dl), -delta);
   const float sg = (dh != 0.f) ? dh : dl;  // exact sign of u_i - u_j
-  t = (sg == 0.f) ? 0.f : copysignf(r, sg);
+  // r * sign(sg): flip r's sign bit by sg's; an exact tie contributes 0
+  const float rs = __int_as_float(__float_as_int(r) ^ (__float_as_int(sg) & 0x80000000));
+  t = (sg == 0.f) ? 0.f : rs;
 }
 
 // Generic k: distance and dd/dy_i (= T[2R_c - 2]) with exact rank comparisons.
@@ -227,29 +230,6 @@ __device__ __forceinline__ void load4(const IterParams& Q, int64_t off, float (&
   }
 }
 
-// Sums a[0..15] over the 32 lanes of a warp by recursive halving; lane l
-// returns the total of entry rev4(l & 15) (bits 0..3 of l reversed).
-__device__ __forceinline__ float reduce16(float (&a)[16], int lane) {
-#pragma unroll
-  for (int s = 0; s < 4; ++s) {
-    const int h = 8 >> s, x = 1 << s;
-    const bool upper = (lane & x) != 0;
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      if (i < h) {
-        const float send = upper ? a[i] : a[i + h];
-        const float keep = upper ? a[i + h] : a[i];
-        a[i] = keep + __shfl_xor_sync(FULL_MASK, send, x);
-      }
-    }
-  }
-  return a[0] + __shfl_xor_sync(FULL_MASK, a[0], 16);
-}
-
-__device__ __forceinline__ int rev4(int l) {
-  return ((l & 1) << 3) | ((l & 2) << 1) | ((l & 4) >> 1) | ((l & 8) >> 3);
-}
-
 __device__ __forceinline__ void block_add_stress(double v, double* dst) {
   __shared__ double s_red[FUSED_THREADS / 32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -264,77 +244,277 @@ __device__ __forceinline__ void block_add_stress(double v, double* dst) {
   }
 }
 
-// k = 2 fused kernel.  Persistent CTAs walk tiles t = blockIdx.x + q gridDim.x.
-template <int DT, bool GRAD>
-__global__ void __launch_bounds__(FUSED_THREADS) k_fused2(const IterParams Q, int64_t ntiles) {
-  __shared__ float s_col[FUSED_THREADS / 32][TILE];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const float c2 = Q.tab.c2;
-  double Sd = 0.0;
-  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    int I, J;
-    tile_decode(t, Q.tiles, I, J);
-    const int64_t i0 = (int64_t)I * TILE, j0 = (int64_t)J * TILE;
-    float2 uc[4];
-    float sc[4];
-    int64_t gjv[4];
+// k = 2 fused kernel, fed by a bulk-copy pipeline.
+//
+// CTA = 8 consumer warps + 1 producer warp.  A CTA owns a contiguous range of
+// tiles (so consecutive tiles usually share the tile-row I).  Each tile is
+// streamed as two chunks of 64 rows x 128 columns (one or two planes); the
+// producer's elected lane keeps S chunks in flight with cp.async.bulk into a
+// shared-memory ring (full/empty mbarriers, bounded waits).  Consumer warp w
+// takes rows w*8 .. w*8+7 of each chunk, lane l columns 4l .. 4l+3.
+//
+// Per element: r = 2^{1-nu}|u_i - u_j| - delta, S += r^2, t = r sign(u_i - u_j)
+// with the exact sign of the TwoSum pairs; t adds to row i and subtracts from
+// column j.  Row sums stay in registers while the tile-row does not change;
+// column sums of a tile meet in shared memory behind one named barrier.
+constexpr int CONSUMER_WARPS = 8;
+constexpr int PIPE_THREADS = (CONSUMER_WARPS + 1) * 32;
+constexpr int CHUNK_ROWS = 64;
+
+template <int DT>
+struct PipeCfg {
+  static constexpr int planes = DT == GINI_BF16X2 ? 2 : 1;
+  static constexpr int esize = DT == GINI_F32 ? 4 : (DT == GINI_FP8E4M3 ? 1 : 2);
+  static constexpr int plane_bytes = CHUNK_ROWS * TILE * esize;
+  static constexpr int stage_bytes = planes * plane_bytes;
+  static constexpr int stages_raw = (96 * 1024) / stage_bytes;
+  static constexpr int stages = stages_raw > 8 ? 8 : stages_raw;
+  static constexpr int smem = stages * stage_bytes;
+};
+
+// r * sign(sg) with sign(0) = 0, on the FMA pipe: a saturating multiply by
+// 2^150 maps any non-zero float to exactly 1 (the positive or the negative
+// part), zero to 0.
+__device__ __forceinline__ float times_sign(float r, float sg) {
+  const float a = sg * 0x1p126f;
+  const float p = __saturatef(a * 0x1p24f);
+  const float q = __saturatef(-a * 0x1p24f);
+  return fmaf(r, p, -(r * q));
+}
+
+// Sums a[0..7] over the 32 lanes; lane l returns the total of entry
+// rev3(l & 7).
+__device__ __forceinline__ float reduce8(float (&a)[8], int lane) {
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      gjv[c] = j0 + 4 * lane + c;
-      const int64_t gj = gjv[c] < Q.n ? gjv[c] : Q.n - 1;
-      uc[c] = Q.P[gj];
-      sc[c] = (DT == GINI_FP8E4M3) ? Q.col_scale[gj] : 1.f;
-    }
-    const int rbase = warp * 16;
-    const int64_t gil = i0 + rbase + (lane & 15);
-    const float2 url = Q.P[gil < Q.n ? gil : Q.n - 1];
-    const int64_t tbase = t * (int64_t)(TILE * TILE);
-    float colacc[4] = {0.f, 0.f, 0.f, 0.f};
-    float rowacc[16];
-    float S = 0.f;
+  for (int s = 0; s < 3; ++s) {
+    const int h = 4 >> s, x = 1 << s;
+    const bool upper = (lane & x) != 0;
 #pragma unroll
-    for (int rr = 0; rr < 16; ++rr) {
-      const int rl = rbase + rr;
-      const int64_t gi = i0 + rl;
-      const float2 ur = make_float2(__shfl_sync(FULL_MASK, url.x, rr),
-                                    __shfl_sync(FULL_MASK, url.y, rr));
-      float dl[4];
-      load4<DT>(Q, tbase + (int64_t)rl * TILE + 4 * lane, dl, sc);
-      float ra = 0.f;
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const bool ok = gi < Q.n && gjv[c] < Q.n && (I != J || rl < 4 * lane + c);
-        float r, tt;
-        pair2(ur, uc[c], c2, dl[c], r, tt);
-        r = ok ? r : 0.f;
-        tt = ok ? tt : 0.f;
-        S = fmaf(r, r, S);
-        ra += tt;
-        colacc[c] -= tt;
+    for (int i = 0; i < 4; ++i) {
+      if (i < h) {
+        const float send = upper ? a[i] : a[i + h];
+        const float keep = upper ? a[i + h] : a[i];
+        a[i] = keep + __shfl_xor_sync(FULL_MASK, send, x);
       }
-      rowacc[rr] = ra;
-    }
-    Sd += (double)S;
-    if (GRAD) {
-      const float rs = reduce16(rowacc, lane);
-      if (lane < 16) {
-        const int64_t gi = i0 + rbase + rev4(lane);
-        if (gi < Q.n) atomicAdd(Q.h + gi, rs);
-      }
-#pragma unroll
-      for (int c = 0; c < 4; ++c) s_col[warp][4 * lane + c] = colacc[c];
-      __syncthreads();
-      if (threadIdx.x < TILE) {
-        float s = 0.f;
-#pragma unroll
-        for (int w = 0; w < FUSED_THREADS / 32; ++w) s += s_col[w][threadIdx.x];
-        const int64_t gj = j0 + threadIdx.x;
-        if (gj < Q.n) atomicAdd(Q.h + gj, s);
-      }
-      __syncthreads();
     }
   }
-  block_add_stress(Sd, Q.stress);
+  float v = a[0] + __shfl_xor_sync(FULL_MASK, a[0], 8);
+  return v + __shfl_xor_sync(FULL_MASK, v, 16);
+}
+
+__device__ __forceinline__ int rev3(int l) { return ((l & 1) << 2) | (l & 2) | ((l & 4) >> 2); }
+
+template <int DT>
+__device__ __forceinline__ void load4_smem(const unsigned char* stage, int rr, int lane,
+                                           float (&d)[4], const float (&sc)[4]) {
+  using C = PipeCfg<DT>;
+  const int off = rr * TILE + 4 * lane;  // element offset inside a plane
+  if (DT == GINI_F32) {
+    const float4 v = *reinterpret_cast<const float4*>(stage + off * 4);
+    d[0] = v.x; d[1] = v.y; d[2] = v.z; d[3] = v.w;
+  } else if (DT == GINI_BF16 || DT == GINI_BF16X2) {
+    const uint2 h = *reinterpret_cast<const uint2*>(stage + off * 2);
+    d[0] = bf16_bits_to_float(h.x & 0xffffu);
+    d[1] = __uint_as_float(h.x & 0xffff0000u);
+    d[2] = bf16_bits_to_float(h.y & 0xffffu);
+    d[3] = __uint_as_float(h.y & 0xffff0000u);
+    if (DT == GINI_BF16X2) {
+      const uint2 l = *reinterpret_cast<const uint2*>(stage + C::plane_bytes + off * 2);
+      d[0] += bf16_bits_to_float(l.x & 0xffffu);
+      d[1] += __uint_as_float(l.x & 0xffff0000u);
+      d[2] += bf16_bits_to_float(l.y & 0xffffu);
+      d[3] += __uint_as_float(l.y & 0xffff0000u);
+    }
+  } else {
+    const uint32_t q = *reinterpret_cast<const uint32_t*>(stage + off);
+    const __half2_raw lo = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(q & 0xffffu), __NV_E4M3);
+    const __half2_raw hi = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(q >> 16), __NV_E4M3);
+    const float2 a = __half22float2(__half2(lo));
+    const float2 b = __half22float2(__half2(hi));
+    d[0] = a.x * sc[0]; d[1] = a.y * sc[1]; d[2] = b.x * sc[2]; d[3] = b.y * sc[3];
+  }
+}
+
+template <int DT, bool GRAD, bool MASKED>
+__device__ __forceinline__ void chunk_compute(const unsigned char* stage, int rbase, int lane,
+                                              const float2 (&uc)[4], float2 url, float c2,
+                                              const float (&sc)[4], float& S, float (&colacc)[4],
+                                              float (&rowv)[8], int64_t gi0, int64_t gj0,
+                                              int64_t n, bool diag, int rl0) {
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const float2 ur = make_float2(__shfl_sync(FULL_MASK, url.x, q),
+                                  __shfl_sync(FULL_MASK, url.y, q));
+    float dl[4];
+    load4_smem<DT>(stage, rbase + q, lane, dl, sc);
+    float ra = 0.f;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const float dh = ur.x - uc[c].x, dlo = ur.y - uc[c].y;
+      const float sg = (dh != 0.f) ? dh : dlo;  // exact sign of u_i - u_j
+      float r = fmaf(c2, fabsf(dh + dlo), -dl[c]);
+      if (MASKED) {
+        const int rl = rl0 + q, cl = 4 * lane + c;
+        const bool ok = (gi0 + q < n) && (gj0 + c < n) && (!diag || rl < cl);
+        r = ok ? r : 0.f;
+      }
+      S = fmaf(r, r, S);
+      if (GRAD) {
+        const float t = times_sign(r, sg);
+        ra += t;
+        colacc[c] -= t;
+      }
+    }
+    rowv[q] = ra;
+  }
+}
+
+template <int DT, bool GRAD>
+__global__ void __launch_bounds__(PIPE_THREADS) k_fused2(const IterParams Q, int64_t ntiles) {
+  using C = PipeCfg<DT>;
+  constexpr int S = C::stages;
+  extern __shared__ __align__(128) unsigned char s_stage[];
+  __shared__ __align__(8) uint64_t bar_full[S];
+  __shared__ __align__(8) uint64_t bar_empty[S];
+  __shared__ float s_colw[2][CONSUMER_WARPS][TILE];
+  __shared__ double s_red[CONSUMER_WARPS];
+  __shared__ int s_abort;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t t_begin = ntiles * blockIdx.x / gridDim.x;
+  const int64_t t_end = ntiles * (blockIdx.x + 1) / gridDim.x;
+  const int nchunks = (int)(t_end - t_begin) * 2;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&bar_full[s], 1);
+      mbar_init(&bar_empty[s], CONSUMER_WARPS);
+    }
+    s_abort = 0;
+    mbar_init_fence();
+  }
+  __syncthreads();
+  volatile int* abort = &s_abort;
+
+  if (warp == CONSUMER_WARPS) {
+    // ---------------------------------------------------------- producer --
+    if (lane == 0) {
+      const unsigned char* base = reinterpret_cast<const unsigned char*>(Q.delta);
+      int issued = 0;
+      for (int c = 0; c < nchunks; ++c) {
+        const int s = c % S, use = c / S;
+        if (use > 0 && !mbar_wait_bounded(&bar_empty[s], (use - 1) & 1, abort)) {
+          raise_error(Q.err, ERR_TIMEOUT);
+          *abort = 1;
+          break;
+        }
+        const int64_t t = t_begin + c / 2;
+        const int64_t eoff = t * (int64_t)(TILE * TILE) + (int64_t)(c & 1) * CHUNK_ROWS * TILE;
+        unsigned char* dst = s_stage + s * C::stage_bytes;
+        mbar_arrive_expect_tx(&bar_full[s], C::stage_bytes);
+        bulk_copy_g2s(dst, base + eoff * C::esize, C::plane_bytes, &bar_full[s]);
+        if (C::planes == 2)
+          bulk_copy_g2s(dst + C::plane_bytes, base + (Q.plane + eoff) * C::esize, C::plane_bytes,
+                        &bar_full[s]);
+        issued = c + 1;
+      }
+      // Copies still in flight must land before this CTA's shared memory can
+      // be released (normally the consumers have waited for all of them).
+      for (int c = (issued > S ? issued - S : 0); c < issued; ++c)
+        mbar_wait_bounded(&bar_full[c % S], (c / S) & 1, nullptr);
+    }
+    return;
+  }
+
+  // ------------------------------------------------------------ consumers --
+  const float c2 = Q.tab.c2;
+  const int64_t n = Q.n;
+  double Sd = 0.0;
+  float rowacc0 = 0.f, rowacc1 = 0.f;  // lane l < 8: rows rev3(l) of chunk 0 and 1
+  int curI = -1;
+  float2 uc[4];
+  float sc[4] = {1.f, 1.f, 1.f, 1.f};
+  float colacc[4] = {0.f, 0.f, 0.f, 0.f};
+  int I = 0, J = 0;
+  for (int c = 0; c < nchunks; ++c) {
+    const int s = c % S, h = c & 1;
+    const int64_t t = t_begin + c / 2;
+    if (h == 0) {
+      tile_decode(t, Q.tiles, I, J);
+      if (GRAD && I != curI) {
+        if (curI >= 0 && lane < 8) {
+          const int64_t gi = (int64_t)curI * TILE + warp * 8 + rev3(lane);
+          if (gi < n) atomicAdd(Q.h + gi, rowacc0);
+          if (gi + CHUNK_ROWS < n) atomicAdd(Q.h + gi + CHUNK_ROWS, rowacc1);
+        }
+        rowacc0 = rowacc1 = 0.f;
+        curI = I;
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int64_t gj = (int64_t)J * TILE + 4 * lane + q;
+        const int64_t g = gj < n ? gj : n - 1;
+        uc[q] = Q.P[g];
+        if (DT == GINI_FP8E4M3) sc[q] = Q.col_scale[g];
+        colacc[q] = 0.f;
+      }
+    }
+    const int rl0 = h * CHUNK_ROWS + warp * 8;
+    const int64_t gi0 = (int64_t)I * TILE + rl0;
+    const int64_t gil = gi0 + (lane & 7);
+    const float2 url = Q.P[gil < n ? gil : n - 1];
+    const int64_t gj0 = (int64_t)J * TILE + 4 * lane;
+    const bool masked = (I == J) || ((int64_t)I * TILE + TILE > n) || ((int64_t)J * TILE + TILE > n);
+
+    if (!mbar_wait_bounded(&bar_full[s], (c / S) & 1, abort)) {
+      raise_error(Q.err, ERR_TIMEOUT);
+      *abort = 1;
+    }
+    const unsigned char* stage = s_stage + s * C::stage_bytes;
+    float rowv[8];
+    float Sf = 0.f;
+    if (masked)
+      chunk_compute<DT, GRAD, true>(stage, warp * 8, lane, uc, url, c2, sc, Sf, colacc, rowv,
+                                    gi0, gj0, n, I == J, rl0);
+    else
+      chunk_compute<DT, GRAD, false>(stage, warp * 8, lane, uc, url, c2, sc, Sf, colacc, rowv,
+                                     gi0, gj0, n, false, rl0);
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&bar_empty[s]);
+    Sd += (double)Sf;
+    if (GRAD) {
+      const float rs = reduce8(rowv, lane);
+      if (h) rowacc1 += rs;
+      else rowacc0 += rs;
+      if (h == 1) {
+        float* cw = s_colw[(c >> 1) & 1][warp];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) cw[4 * lane + q] = colacc[q];
+        named_bar_sync(CONSUMER_WARPS * 32);
+        if (threadIdx.x < TILE) {
+          float v = 0.f;
+#pragma unroll
+          for (int w = 0; w < CONSUMER_WARPS; ++w) v += s_colw[(c >> 1) & 1][w][threadIdx.x];
+          const int64_t gj = (int64_t)J * TILE + threadIdx.x;
+          if (gj < n) atomicAdd(Q.h + gj, v);
+        }
+      }
+    }
+  }
+  if (GRAD && curI >= 0 && lane < 8) {
+    const int64_t gi = (int64_t)curI * TILE + warp * 8 + rev3(lane);
+    if (gi < n) atomicAdd(Q.h + gi, rowacc0);
+    if (gi + CHUNK_ROWS < n) atomicAdd(Q.h + gi + CHUNK_ROWS, rowacc1);
+  }
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) Sd += __shfl_xor_sync(FULL_MASK, Sd, o);
+  if (lane == 0) s_red[warp] = Sd;
+  named_bar_sync(CONSUMER_WARPS * 32);
+  if (threadIdx.x == 0) {
+    double v = 0.0;
+    for (int w = 0; w < CONSUMER_WARPS; ++w) v += s_red[w];
+    atomicAdd(Q.stress, v);
+  }
 }
 
 // Generic k (3..8) fused kernel: the tile's row and column points are staged
@@ -657,10 +837,23 @@ static void launch_fused_dt(int k, const IterParams& Q, cudaStream_t s) {
   const int64_t cap = (int64_t)sm_count() * 4;
   const unsigned g = (unsigned)(ntiles < cap ? ntiles : cap);
   switch (k) {
-    case 2:
+    case 2: {
+      using C = PipeCfg<DT>;
+      static int per_sm = 0;  // resident CTAs per SM for this instance
+      if (!per_sm) {
+        cudaFuncSetAttribute(k_fused2<DT, GRAD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             C::smem);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused2<DT, GRAD>,
+                                                          PIPE_THREADS, C::smem) != cudaSuccess ||
+            per_sm < 1)
+          per_sm = 1;
+      }
+      const int64_t cap2 = (int64_t)sm_count() * per_sm;
+      const unsigned g2 = (unsigned)(ntiles < cap2 ? ntiles : cap2);
       gini_count_launch(1);
-      k_fused2<DT, GRAD><<<g, FUSED_THREADS, 0, s>>>(Q, ntiles);
+      k_fused2<DT, GRAD><<<g2, PIPE_THREADS, C::smem, s>>>(Q, ntiles);
       break;
+    }
     case 3: launch_fusedk<3, DT, GRAD>(g, Q, ntiles, s); break;
     case 4: launch_fusedk<4, DT, GRAD>(g, Q, ntiles, s); break;
     case 5: launch_fusedk<5, DT, GRAD>(g, Q, ntiles, s); break;

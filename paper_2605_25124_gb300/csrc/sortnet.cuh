@@ -35,6 +35,20 @@ __device__ __forceinline__ void cas(T& a, T& b) {
   b = hi;
 }
 
+// Cross-lane exchange: the lower lane keeps min(v, o), the upper max(v, o).
+// For floats this is written s * min(s*v, s*o) with s = +1 / -1: one min on
+// the (half-rate) ALU pipe and three sign multiplies on the FMA pipe, instead
+// of a min, a max and a select all on the ALU pipe.  Exact: multiplying by
+// -1 only flips the sign bit.
+__device__ __forceinline__ float keep_lo_hi(float v, float o, bool lower) {
+  const float s = lower ? 1.f : -1.f;
+  return s * fminf(s * v, s * o);
+}
+__device__ __forceinline__ unsigned long long keep_lo_hi(unsigned long long v,
+                                                         unsigned long long o, bool lower) {
+  return lower ? kmin(v, o) : kmax(v, o);
+}
+
 template <int E, int L, typename T>
 __device__ __forceinline__ void seg_bitonic_sort(T (&v)[E], int ls) {
   static_assert((E & (E - 1)) == 0 && (L & (L - 1)) == 0 && L <= 32 && E >= 2, "powers of two");
@@ -55,8 +69,8 @@ __device__ __forceinline__ void seg_bitonic_sort(T (&v)[E], int ls) {
         // partner lane's mirrored registers: E-1-t pairs with t
         T a = __shfl_xor_sync(FULL_MASK, v[E - 1 - t], mask);
         T b = __shfl_xor_sync(FULL_MASK, v[t], mask);
-        v[t] = lower ? kmin(v[t], a) : kmax(v[t], a);
-        v[E - 1 - t] = lower ? kmin(v[E - 1 - t], b) : kmax(v[E - 1 - t], b);
+        v[t] = keep_lo_hi(v[t], a, lower);
+        v[E - 1 - t] = keep_lo_hi(v[E - 1 - t], b, lower);
       }
     }
     // half-cleaners: i <-> i ^ jj
@@ -68,7 +82,7 @@ __device__ __forceinline__ void seg_bitonic_sort(T (&v)[E], int ls) {
 #pragma unroll
         for (int t = 0; t < E; ++t) {
           T o = __shfl_xor_sync(FULL_MASK, v[t], mask);
-          v[t] = lower ? kmin(v[t], o) : kmax(v[t], o);
+          v[t] = keep_lo_hi(v[t], o, lower);
         }
       } else {
 #pragma unroll

@@ -190,6 +190,9 @@ WORKLOADS = {
                          iters=200, seed=SEED_BASE + 4),
     "image-n20000-p784": dict(kind="image_like", n=20000, p=784, k=2,
                               nu=[2.0], iters=200, seed=SEED_BASE + 5),
+    # smaller case of the same kind for profiler captures (BF16 Delta > L2)
+    "image-n12000-p784": dict(kind="image_like", n=12000, p=784, k=2,
+                              nu=[2.0], iters=200, seed=SEED_BASE + 6),
 }
 
 

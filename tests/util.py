@@ -24,9 +24,29 @@ def untile(flat, n, planes=1):
 
 
 def rel_err(got, ref, floor=0.0):
+    """max |got - ref| / max(|ref|, floor); entries equal on both sides count 0."""
     got = np.asarray(got, dtype=np.float64)
     ref = np.asarray(ref, dtype=np.float64)
-    return np.max(np.abs(got - ref) / np.maximum(np.abs(ref), floor)) if ref.size else 0.0
+    if not ref.size:
+        return 0.0
+    den = np.maximum(np.abs(ref), floor)
+    err = np.abs(got - ref)
+    return float(np.max(np.where(err == 0, 0.0, err / np.where(den == 0, 1.0, den))))
+
+
+def fro_rel(got, ref):
+    """Norm-wise relative error ||got - ref||_F / ||ref||_F."""
+    got = np.asarray(got, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    return float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+
+
+# Storage tolerances of a dissimilarity matrix against the FP64 oracle:
+# per entry, round-to-nearest of an 8-bit significand (bf16) is within 2^-8;
+# hi + lo within 2^-16; plus 1e-6 for the FP32 build.  Norm-wise (Frobenius),
+# BF16 within 2e-3 and hi + lo within 1e-5.
+ENTRY_TOL = {"f32": 1e-5, "bf16": 2.0 ** -8 + 1e-6, "bf16x2": 2.0 ** -16 + 1e-6}
+NORM_TOL = {"f32": 1e-5, "bf16": 2e-3, "bf16x2": 1e-5}
 
 
 def quantize(full, dtype, col_scale=None):
