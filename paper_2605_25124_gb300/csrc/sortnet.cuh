@@ -36,13 +36,10 @@ __device__ __forceinline__ void cas(T& a, T& b) {
 }
 
 // Cross-lane exchange: the lower lane keeps min(v, o), the upper max(v, o).
-// For floats this is written s * min(s*v, s*o) with s = +1 / -1: one min on
-// the (half-rate) ALU pipe and three sign multiplies on the FMA pipe, instead
-// of a min, a max and a select all on the ALU pipe.  Exact: multiplying by
-// -1 only flips the sign bit.
+// (Rewriting it as s * min(s*v, s*o), s = +-1, moves two of the three
+// operations off the ALU pipe but raised register use and measured slower.)
 __device__ __forceinline__ float keep_lo_hi(float v, float o, bool lower) {
-  const float s = lower ? 1.f : -1.f;
-  return s * fminf(s * v, s * o);
+  return lower ? fminf(v, o) : fmaxf(v, o);
 }
 __device__ __forceinline__ unsigned long long keep_lo_hi(unsigned long long v,
                                                          unsigned long long o, bool lower) {

@@ -81,7 +81,7 @@ def test_split_bf16_reaches_fp32_final_stress(G):
     h = hs.cpu().numpy()
     print(f"hi-only 160 + hi+lo 40: final stress {float(sched):.6g} vs FP32 {float(f32):.6g} "
           f"(rel {abs(float(sched) - float(f32)) / float(f32):.2e})")
-    assert np.all(np.diff(h) <= 1e-12) and h[-1] < 0.1 * h[0]
+    assert np.all(np.diff(h) <= 1e-7 * h[0]) and h[-1] < 0.1 * h[0]  # FP32 wobble at rest
 
 
 def test_fit_resume_and_zero_iterations(G):
