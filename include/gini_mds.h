@@ -171,6 +171,33 @@ int gini_stress_grad(const float* Y_dev, int64_t n, int k, double nu, const void
                      double sum_delta2, double* stress_dev, float* grad_dev, void* ws,
                      size_t ws_bytes, void* stream);
 
+/* gini_stress_grad for callers that cannot allocate device memory.  The paper
+ * has no counterpart; this is a library service.  Some callers may not call
+ * cudaMalloc at all: code recording a CUDA graph (allocation is not allowed
+ * while a stream is being captured), plugins whose host application owns every
+ * byte of device memory through its own pool, and latency-bound loops that
+ * cannot afford the device-wide synchronisation an allocation or free implies.
+ * They pass inputs and outputs exactly as for gini_stress_grad, but no
+ * workspace: the scratch space is a fixed 8 MiB array inside the library, which
+ * every GPU that loads the library holds until the process exits.
+ *   - Sizes whose gini_workspace_size(GINI_OP_STRESS, n, 0, k, 0) exceeds 8 MiB
+ *     (about 520,000 points at k = 2, 230,000 at k = 3) return GINI_ENOMEM
+ *     before anything is enqueued.
+ *   - The first call on a device looks up the array's device address with that
+ *     device current; make that first call before any stream capture.
+ *   - Nothing is allocated: no cudaMalloc, no cudaFree, no allocating library
+ *     routine.  The array keeps the previous call's contents; the call clears
+ *     what must start at zero.
+ *   - All calls share the one array, so calls whose work overlaps on the GPU
+ *     (different streams, or host threads without ordering) race and corrupt
+ *     each other's results.  Order them on one stream.
+ *   - There is no workspace for gini_check: a device-side error (non-finite Y,
+ *     an expired bounded wait) is reported by writing NaN to *stress_dev. */
+int gini_stress_grad_noalloc(const float* Y_dev, int64_t n, int k, double nu,
+                             const void* delta_dev, int layout, int dtype, int64_t ldd,
+                             const float* col_scale_dev, double sum_delta2, double* stress_dev,
+                             float* grad_dev, void* stream);
+
 /* Arguments of gini_mds_fit. */
 typedef struct {
   int64_t n;                  /* points, >= 2 */

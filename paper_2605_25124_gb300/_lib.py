@@ -49,6 +49,8 @@ SIGNATURES = {
     "gini_stress_grad": (_c.c_int, [_vp, _i64, _c.c_int, _c.c_double, _vp, _c.c_int, _c.c_int,
                                     _i64, _vp, _c.c_double, _vp, _vp, _vp, _c.c_size_t, _vp]),
     "gini_mds_fit": (_c.c_int, [_c.POINTER(FitArgs), _vp, _c.c_size_t, _vp]),
+    "gini_stress_grad_noalloc": (_c.c_int, [_vp, _i64, _c.c_int, _c.c_double, _vp, _c.c_int,
+                                            _c.c_int, _i64, _vp, _c.c_double, _vp, _vp, _vp]),
     "gini_default_step": (_c.c_double, [_i64, _c.c_int, _c.c_double, _c.c_double, _c.c_double]),
 }
 
