@@ -53,11 +53,15 @@ struct IterParams {
 // ------------------------------------------------------------ point prep ---
 
 template <int K>
-__global__ void k_prep(const float* __restrict__ Y, int64_t n, float2* __restrict__ P,
-                       unsigned* err) {
+__global__ void k_prep(const float* __restrict__ Y, int64_t n, int64_t npad,
+                       float2* __restrict__ P, unsigned* err) {
   constexpr int NP = K * (K - 1) / 2;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   bool bad = false;
+  if (i >= n && i < npad) {
+#pragma unroll
+    for (int p = 0; p < NP; ++p) P[i * NP + p] = make_float2(0.f, 0.f);
+  }
   if (i < n) {
     float y[K];
 #pragma unroll
@@ -266,21 +270,16 @@ struct PipeCfg {
   static constexpr int planes = DT == GINI_BF16X2 ? 2 : 1;
   static constexpr int esize = DT == GINI_F32 ? 4 : (DT == GINI_FP8E4M3 ? 1 : 2);
   static constexpr int plane_bytes = CHUNK_ROWS * TILE * esize;
-  static constexpr int stage_bytes = planes * plane_bytes;
-  static constexpr int stages_raw = (96 * 1024) / stage_bytes;
+  // after the planes: the chunk's 64 row points and the tile's 128 column
+  // points (u_i as (hi, lo) pairs), copied with the dissimilarities
+  static constexpr int urow_off = planes * plane_bytes;
+  static constexpr int ucol_off = urow_off + CHUNK_ROWS * 8;
+  static constexpr int stage_bytes = ucol_off + TILE * 8;
+  // 104 KB of stages + ~8.5 KB static per CTA keeps two CTAs on an SM
+  static constexpr int stages_raw = (104 * 1024) / stage_bytes;
   static constexpr int stages = stages_raw > 8 ? 8 : stages_raw;
   static constexpr int smem = stages * stage_bytes;
 };
-
-// r * sign(sg) with sign(0) = 0, on the FMA pipe: a saturating multiply by
-// 2^150 maps any non-zero float to exactly 1 (the positive or the negative
-// part), zero to 0.
-__device__ __forceinline__ float times_sign(float r, float sg) {
-  const float a = sg * 0x1p126f;
-  const float p = __saturatef(a * 0x1p24f);
-  const float q = __saturatef(-a * 0x1p24f);
-  return fmaf(r, p, -(r * q));
-}
 
 // Sums a[0..7] over the 32 lanes; lane l returns the total of entry
 // rev3(l & 7).
@@ -335,37 +334,60 @@ __device__ __forceinline__ void load4_smem(const unsigned char* stage, int rr, i
   }
 }
 
+// One chunk row block of a consumer warp: 8 rows x 4 columns per lane, two
+// columns per packed f32x2 instruction.  With s = u_i - u_j and
+// sigma = sign(s) in {-1, 0, 1} (exact, see below): |s| = s sigma, the
+// residual r = c2 |s| - delta and t = r sigma.  The kernel carries
+// r' = -r = delta - c2 |s| and t' = -t, so no negations are needed:
+// S += r'^2, the row sum collects t' (negated when flushed) and the column
+// sum, which needs -t, collects t' directly.
+//   sigma: a = fma(dh, 2^64, dl) has the sign of u_i - u_j (dl cannot
+//   outweigh a non-zero dh; a = dl exactly when dh = 0), and
+//   sat(a 2^150) - sat(-a 2^150) maps it to exactly -1, 0 or 1.
 template <int DT, bool GRAD, bool MASKED>
 __device__ __forceinline__ void chunk_compute(const unsigned char* stage, int rbase, int lane,
-                                              const float2 (&uc)[4], float2 url, float c2,
-                                              const float (&sc)[4], float& S, float (&colacc)[4],
-                                              float (&rowv)[8], int64_t gi0, int64_t gj0,
-                                              int64_t n, bool diag, int rl0) {
+                                              const float2 (&nuh)[2], const float2 (&nul)[2],
+                                              const float2* urow, float c2, const float (&sc)[4],
+                                              float2& S2, float2 (&col2)[2], float (&rowv)[8],
+                                              int64_t gi0, int64_t gj0, int64_t n, bool diag,
+                                              int rl0) {
+  const float2 k64 = make_float2(0x1p64f, 0x1p64f);
+  const float2 k126 = make_float2(0x1p126f, 0x1p126f);
+  const float2 m1 = make_float2(-1.f, -1.f);
+  const float2 nc2 = make_float2(-c2, -c2);
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
-    const float2 ur = make_float2(__shfl_sync(FULL_MASK, url.x, q),
-                                  __shfl_sync(FULL_MASK, url.y, q));
+    const float2 ur = urow[rbase + q];  // same address in every lane: broadcast
+    const float2 uh2 = make_float2(ur.x, ur.x), ul2 = make_float2(ur.y, ur.y);
     float dl[4];
     load4_smem<DT>(stage, rbase + q, lane, dl, sc);
-    float ra = 0.f;
+    float2 row2 = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const float dh = ur.x - uc[c].x, dlo = ur.y - uc[c].y;
-      const float sg = (dh != 0.f) ? dh : dlo;  // exact sign of u_i - u_j
-      float r = fmaf(c2, fabsf(dh + dlo), -dl[c]);
+    for (int p = 0; p < 2; ++p) {
+      const float2 d2 = make_float2(dl[2 * p], dl[2 * p + 1]);
+      const float2 dh = __fadd2_rn(uh2, nuh[p]);
+      const float2 dlo = __fadd2_rn(ul2, nul[p]);
+      const float2 s2 = __fadd2_rn(dh, dlo);
+      const float2 b2 = __fmul2_rn(__ffma2_rn(dh, k64, dlo), k126);
+      const float2 pp = make_float2(__saturatef(b2.x * 0x1p24f), __saturatef(b2.y * 0x1p24f));
+      const float2 qq = make_float2(__saturatef(-b2.x * 0x1p24f), __saturatef(-b2.y * 0x1p24f));
+      const float2 sig = __ffma2_rn(qq, m1, pp);
+      float2 rp = __ffma2_rn(nc2, __fmul2_rn(s2, sig), d2);  // r' = delta - c2 |s|
       if (MASKED) {
-        const int rl = rl0 + q, cl = 4 * lane + c;
-        const bool ok = (gi0 + q < n) && (gj0 + c < n) && (!diag || rl < cl);
-        r = ok ? r : 0.f;
+        const int rl = rl0 + q, cl = 4 * lane + 2 * p;
+        const bool ok0 = (gi0 + q < n) && (gj0 + 2 * p < n) && (!diag || rl < cl);
+        const bool ok1 = (gi0 + q < n) && (gj0 + 2 * p + 1 < n) && (!diag || rl < cl + 1);
+        rp.x = ok0 ? rp.x : 0.f;
+        rp.y = ok1 ? rp.y : 0.f;
       }
-      S = fmaf(r, r, S);
+      S2 = __ffma2_rn(rp, rp, S2);
       if (GRAD) {
-        const float t = times_sign(r, sg);
-        ra += t;
-        colacc[c] -= t;
+        const float2 tp = __fmul2_rn(rp, sig);  // t' = -t
+        row2 = __fadd2_rn(row2, tp);
+        col2[p] = __fadd2_rn(col2[p], tp);
       }
     }
-    rowv[q] = ra;
+    rowv[q] = -(row2.x + row2.y);
   }
 }
 
@@ -409,13 +431,20 @@ __global__ void __launch_bounds__(PIPE_THREADS) k_fused2(const IterParams Q, int
           break;
         }
         const int64_t t = t_begin + c / 2;
-        const int64_t eoff = t * (int64_t)(TILE * TILE) + (int64_t)(c & 1) * CHUNK_ROWS * TILE;
+        const int h = c & 1;
+        int I, J;
+        tile_decode(t, Q.tiles, I, J);
+        const int64_t eoff = t * (int64_t)(TILE * TILE) + (int64_t)h * CHUNK_ROWS * TILE;
         unsigned char* dst = s_stage + s * C::stage_bytes;
         mbar_arrive_expect_tx(&bar_full[s], C::stage_bytes);
         bulk_copy_g2s(dst, base + eoff * C::esize, C::plane_bytes, &bar_full[s]);
         if (C::planes == 2)
           bulk_copy_g2s(dst + C::plane_bytes, base + (Q.plane + eoff) * C::esize, C::plane_bytes,
                         &bar_full[s]);
+        // point arrays are padded to whole tiles, so these stay in bounds
+        bulk_copy_g2s(dst + C::urow_off, Q.P + (int64_t)I * TILE + h * CHUNK_ROWS,
+                      CHUNK_ROWS * 8, &bar_full[s]);
+        bulk_copy_g2s(dst + C::ucol_off, Q.P + (int64_t)J * TILE, TILE * 8, &bar_full[s]);
         issued = c + 1;
       }
       // Copies still in flight must land before this CTA's shared memory can
@@ -432,9 +461,10 @@ __global__ void __launch_bounds__(PIPE_THREADS) k_fused2(const IterParams Q, int
   double Sd = 0.0;
   float rowacc0 = 0.f, rowacc1 = 0.f;  // lane l < 8: rows rev3(l) of chunk 0 and 1
   int curI = -1;
-  float2 uc[4];
+  float2 nuh[2], nul[2];               // -u of the lane's 4 columns, packed by pairs
   float sc[4] = {1.f, 1.f, 1.f, 1.f};
-  float colacc[4] = {0.f, 0.f, 0.f, 0.f};
+  float2 col2[2];
+  float2 S2 = make_float2(0.f, 0.f);
   int I = 0, J = 0;
   for (int c = 0; c < nchunks; ++c) {
     const int s = c % S, h = c & 1;
@@ -450,19 +480,18 @@ __global__ void __launch_bounds__(PIPE_THREADS) k_fused2(const IterParams Q, int
         rowacc0 = rowacc1 = 0.f;
         curI = I;
       }
+      if (DT == GINI_FP8E4M3) {
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int64_t gj = (int64_t)J * TILE + 4 * lane + q;
-        const int64_t g = gj < n ? gj : n - 1;
-        uc[q] = Q.P[g];
-        if (DT == GINI_FP8E4M3) sc[q] = Q.col_scale[g];
-        colacc[q] = 0.f;
+        for (int q = 0; q < 4; ++q) {
+          const int64_t gj = (int64_t)J * TILE + 4 * lane + q;
+          sc[q] = Q.col_scale[gj < n ? gj : n - 1];
+        }
       }
+#pragma unroll
+      for (int p = 0; p < 2; ++p) col2[p] = make_float2(0.f, 0.f);
     }
     const int rl0 = h * CHUNK_ROWS + warp * 8;
     const int64_t gi0 = (int64_t)I * TILE + rl0;
-    const int64_t gil = gi0 + (lane & 7);
-    const float2 url = Q.P[gil < n ? gil : n - 1];
     const int64_t gj0 = (int64_t)J * TILE + 4 * lane;
     const bool masked = (I == J) || ((int64_t)I * TILE + TILE > n) || ((int64_t)J * TILE + TILE > n);
 
@@ -471,25 +500,36 @@ __global__ void __launch_bounds__(PIPE_THREADS) k_fused2(const IterParams Q, int
       *abort = 1;
     }
     const unsigned char* stage = s_stage + s * C::stage_bytes;
+    const float2* urow = reinterpret_cast<const float2*>(stage + C::urow_off);
+    {
+      const float4* ucol = reinterpret_cast<const float4*>(stage + C::ucol_off) + 2 * lane;
+      const float4 a = ucol[0], b = ucol[1];  // columns 4l, 4l+1 | 4l+2, 4l+3 as (hi, lo)
+      nuh[0] = make_float2(-a.x, -a.z);
+      nul[0] = make_float2(-a.y, -a.w);
+      nuh[1] = make_float2(-b.x, -b.z);
+      nul[1] = make_float2(-b.y, -b.w);
+    }
     float rowv[8];
-    float Sf = 0.f;
     if (masked)
-      chunk_compute<DT, GRAD, true>(stage, warp * 8, lane, uc, url, c2, sc, Sf, colacc, rowv,
-                                    gi0, gj0, n, I == J, rl0);
+      chunk_compute<DT, GRAD, true>(stage, warp * 8, lane, nuh, nul, urow, c2, sc, S2, col2,
+                                    rowv, gi0, gj0, n, I == J, rl0);
     else
-      chunk_compute<DT, GRAD, false>(stage, warp * 8, lane, uc, url, c2, sc, Sf, colacc, rowv,
-                                     gi0, gj0, n, false, rl0);
+      chunk_compute<DT, GRAD, false>(stage, warp * 8, lane, nuh, nul, urow, c2, sc, S2, col2,
+                                     rowv, gi0, gj0, n, false, rl0);
     __syncwarp();
     if (lane == 0) mbar_arrive(&bar_empty[s]);
-    Sd += (double)Sf;
+    if (h == 1) {  // fold the FP32 partial of each tile into FP64
+      Sd += (double)S2.x + (double)S2.y;
+      S2 = make_float2(0.f, 0.f);
+    }
     if (GRAD) {
       const float rs = reduce8(rowv, lane);
       if (h) rowacc1 += rs;
       else rowacc0 += rs;
       if (h == 1) {
         float* cw = s_colw[(c >> 1) & 1][warp];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) cw[4 * lane + q] = colacc[q];
+        *reinterpret_cast<float4*>(cw + 4 * lane) =
+            make_float4(col2[0].x, col2[0].y, col2[1].x, col2[1].y);
         named_bar_sync(CONSUMER_WARPS * 32);
         if (threadIdx.x < TILE) {
           float v = 0.f;
@@ -701,10 +741,15 @@ using namespace gini;
 extern "C" void gini_set_cuda_error(cudaError_t e);
 
 // Workspace of the iteration ops: header | nacc doubles | point pairs | h.
+// Point pairs are stored for ceil(n / B) * B points (whole tiles, the padding
+// zero-filled) so that bulk copies of a tile's points never leave the array.
+static int64_t padded_points(int64_t n) { return tiles_1d(n) * TILE; }
+
 extern "C" size_t gini_iter_ws_bytes(int64_t n, int k, int nacc) {
   const int np = k * (k - 1) / 2;
   return WS_HEADER + align256(sizeof(double) * (size_t)nacc) +
-         align256(sizeof(float2) * (size_t)n * np) + align256(sizeof(float) * (size_t)n * k);
+         align256(sizeof(float2) * (size_t)padded_points(n) * np) +
+         align256(sizeof(float) * (size_t)n * k);
 }
 
 static IterWs carve(void* ws, int64_t n, int k, int nacc) {
@@ -715,7 +760,7 @@ static IterWs carve(void* ws, int64_t n, int k, int nacc) {
   w.acc = reinterpret_cast<double*>(p);
   p += align256(sizeof(double) * (size_t)nacc);
   w.P = reinterpret_cast<float2*>(p);
-  p += align256(sizeof(float2) * (size_t)n * (k * (k - 1) / 2));
+  p += align256(sizeof(float2) * (size_t)padded_points(n) * (k * (k - 1) / 2));
   w.h = reinterpret_cast<float*>(p);
   return w;
 }
@@ -764,8 +809,9 @@ static int check_common(int64_t n, int k, double nu, const void* delta, int layo
 
 template <int K>
 static void launch_prep(const float* Y, int64_t n, float2* P, unsigned* err, cudaStream_t s) {
+  const int64_t npad = padded_points(n);
   gini_count_launch(1);
-  k_prep<K><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(Y, n, P, err);
+  k_prep<K><<<(unsigned)((npad + 255) / 256), 256, 0, s>>>(Y, n, npad, P, err);
 }
 
 static void prep(int k, const float* Y, int64_t n, float2* P, unsigned* err, cudaStream_t s) {
