@@ -53,7 +53,7 @@ def _args():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-form comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end run")
-    ap.add_argument("--form", default="bf16x2", choices=list(FORMS),
+    ap.add_argument("--form", default="f32", choices=list(FORMS),
                     help="storage of Delta in the timed fits")
     return ap.parse_args()
 

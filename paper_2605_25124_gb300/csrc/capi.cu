@@ -104,17 +104,17 @@ __global__ void k_scale_from_max(unsigned* colmax_bits, int64_t n) {
   reinterpret_cast<float*>(colmax_bits)[j] = sc;
 }
 
-// One thread per stored element of one tile row chunk.
+// Block (x = tile, y = 256-element slice of it); one thread per stored element.
 template <int DT>
 __global__ void k_pack(const float* __restrict__ D, int64_t n, int64_t ldd, int64_t T,
                        int64_t plane, void* __restrict__ out, const float* __restrict__ scale) {
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t ntile = T * (T + 1) / 2;
-  if (e >= ntile * TILE * TILE) return;
-  const int64_t t = e / (TILE * TILE);
-  const int rc = (int)(e % (TILE * TILE));
-  int I, J;
-  tile_decode(t, T, I, J);
+  __shared__ int s_ij[2];
+  const int64_t t = blockIdx.x;
+  if (threadIdx.x == 0) tile_decode(t, T, s_ij[0], s_ij[1]);
+  __syncthreads();
+  const int I = s_ij[0], J = s_ij[1];
+  const int rc = (int)blockIdx.y * blockDim.x + threadIdx.x;
+  const int64_t e = t * (TILE * TILE) + rc;
   const int64_t i = (int64_t)I * TILE + rc / TILE, j = (int64_t)J * TILE + rc % TILE;
   const float v = (i < n && j < n && i < j) ? D[i * ldd + j] : 0.f;
   if (DT == GINI_F32) {
@@ -154,7 +154,7 @@ extern "C" int gini_pack(const float* delta_full_dev, int64_t n, int64_t ldd, in
     }
   }
   if (e == cudaSuccess) {
-    const unsigned blocks = (unsigned)((plane + 255) / 256);
+    const dim3 blocks((unsigned)(T * (T + 1) / 2), TILE * TILE / 256);
     gini_count_launch(1);
     switch (dtype) {
       case GINI_F32: k_pack<GINI_F32><<<blocks, 256, 0, s>>>(delta_full_dev, n, ldd, T, plane, packed_dev, col_scale_dev); break;

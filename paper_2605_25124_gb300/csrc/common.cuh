@@ -46,6 +46,15 @@ __device__ __forceinline__ void tile_decode(int64_t t, int64_t T, int& I, int& J
   J = (int)(t - tile_offset(i, i, T) + i);
 }
 
+// Next tile in row-major upper-triangular order (integer only; GB300's FP64
+// rate is far too low for a sqrt per tile).
+__host__ __device__ __forceinline__ void tile_next(int& I, int& J, int64_t T) {
+  if (++J == T) {
+    ++I;
+    J = I;
+  }
+}
+
 // Offset (in elements) of delta(i, j), i < j, in one plane of the tiled layout.
 __device__ __forceinline__ int64_t tiled_index(int64_t i, int64_t j, int64_t T) {
   int64_t I = i / TILE, J = j / TILE;

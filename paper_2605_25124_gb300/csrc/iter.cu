@@ -140,15 +140,20 @@ __global__ void __launch_bounds__(256) k_full(const IterParams Q) {
     float acc[K];
 #pragma unroll
     for (int c = 0; c < K; ++c) acc[c] = 0.f;
-    float S = 0.f;
-    int cnt = 0;
+    float S = 0.f, Sc = 0.f;  // compensated FP32 sum over the row
     for (int64_t j = (FWD ? i + 1 : 0) + lane; j < Q.n; j += 32) {
       const float dl = __ldcs(D + i * Q.ldd + j);
       if (K == 2) {
         float r, t;
         pair2(Pi[0], Q.P[j], Q.tab.c2, dl, r, t);
-        if (FWD) S = fmaf(r, r, S);
-        else if (j != i) acc[0] += t;
+        if (FWD) {
+          const float y = fmaf(r, r, -Sc);
+          const float tsum = S + y;
+          Sc = (tsum - S) - y;
+          S = tsum;
+        } else if (j != i) {
+          acc[0] += t;
+        }
       } else {
         float yj[K], dw[K];
         float2 Pj[NP];
@@ -158,20 +163,18 @@ __global__ void __launch_bounds__(256) k_full(const IterParams Q) {
         for (int p = 0; p < NP; ++p) Pj[p] = Q.P[j * NP + p];
         const float r = pair_k<K>(yi, yj, Pi, Pj, s_w, dw) - dl;
         if (FWD) {
-          S = fmaf(r, r, S);
+          const float y = fmaf(r, r, -Sc);
+          const float tsum = S + y;
+          Sc = (tsum - S) - y;
+          S = tsum;
         } else if (j != i) {
 #pragma unroll
           for (int c = 0; c < K; ++c) acc[c] = fmaf(r, dw[c], acc[c]);
         }
       }
-      if (FWD && ++cnt == 32) {  // flush FP32 partials into FP64 every 32 terms
-        Sd += (double)S;
-        S = 0.f;
-        cnt = 0;
-      }
     }
     if (FWD) {
-      Sd += (double)S;
+      Sd += (double)S - (double)Sc;
     } else {
 #pragma unroll
       for (int c = 0; c < K; ++c) {
@@ -423,6 +426,8 @@ __global__ void __launch_bounds__(PIPE_THREADS) k_fused2(const IterParams Q, int
     if (lane == 0) {
       const unsigned char* base = reinterpret_cast<const unsigned char*>(Q.delta);
       int issued = 0;
+      int I = 0, J = 0;
+      if (nchunks) tile_decode(t_begin, Q.tiles, I, J);
       for (int c = 0; c < nchunks; ++c) {
         const int s = c % S, use = c / S;
         if (use > 0 && !mbar_wait_bounded(&bar_empty[s], (use - 1) & 1, abort)) {
@@ -432,8 +437,7 @@ __global__ void __launch_bounds__(PIPE_THREADS) k_fused2(const IterParams Q, int
         }
         const int64_t t = t_begin + c / 2;
         const int h = c & 1;
-        int I, J;
-        tile_decode(t, Q.tiles, I, J);
+        if (h == 0 && c > 0) tile_next(I, J, Q.tiles);
         const int64_t eoff = t * (int64_t)(TILE * TILE) + (int64_t)h * CHUNK_ROWS * TILE;
         unsigned char* dst = s_stage + s * C::stage_bytes;
         mbar_arrive_expect_tx(&bar_full[s], C::stage_bytes);
@@ -458,7 +462,7 @@ __global__ void __launch_bounds__(PIPE_THREADS) k_fused2(const IterParams Q, int
   // ------------------------------------------------------------ consumers --
   const float c2 = Q.tab.c2;
   const int64_t n = Q.n;
-  double Sd = 0.0;
+  float Ssum = 0.f, Scomp = 0.f;  // compensated sum of the per-tile FP32 partials
   float rowacc0 = 0.f, rowacc1 = 0.f;  // lane l < 8: rows rev3(l) of chunk 0 and 1
   int curI = -1;
   float2 nuh[2], nul[2];               // -u of the lane's 4 columns, packed by pairs
@@ -466,11 +470,11 @@ __global__ void __launch_bounds__(PIPE_THREADS) k_fused2(const IterParams Q, int
   float2 col2[2];
   float2 S2 = make_float2(0.f, 0.f);
   int I = 0, J = 0;
+  if (nchunks) tile_decode(t_begin, Q.tiles, I, J);
   for (int c = 0; c < nchunks; ++c) {
     const int s = c % S, h = c & 1;
-    const int64_t t = t_begin + c / 2;
     if (h == 0) {
-      tile_decode(t, Q.tiles, I, J);
+      if (c > 0) tile_next(I, J, Q.tiles);
       if (GRAD && I != curI) {
         if (curI >= 0 && lane < 8) {
           const int64_t gi = (int64_t)curI * TILE + warp * 8 + rev3(lane);
@@ -518,8 +522,11 @@ __global__ void __launch_bounds__(PIPE_THREADS) k_fused2(const IterParams Q, int
                                      rowv, gi0, gj0, n, false, rl0);
     __syncwarp();
     if (lane == 0) mbar_arrive(&bar_empty[s]);
-    if (h == 1) {  // fold the FP32 partial of each tile into FP64
-      Sd += (double)S2.x + (double)S2.y;
+    if (h == 1) {  // fold the FP32 partial of each tile (Kahan)
+      const float y = (S2.x + S2.y) - Scomp;
+      const float tsum = Ssum + y;
+      Scomp = (tsum - Ssum) - y;
+      Ssum = tsum;
       S2 = make_float2(0.f, 0.f);
     }
     if (GRAD) {
@@ -546,6 +553,7 @@ __global__ void __launch_bounds__(PIPE_THREADS) k_fused2(const IterParams Q, int
     if (gi < n) atomicAdd(Q.h + gi, rowacc0);
     if (gi + CHUNK_ROWS < n) atomicAdd(Q.h + gi + CHUNK_ROWS, rowacc1);
   }
+  double Sd = (double)Ssum - (double)Scomp;
 #pragma unroll
   for (int o = 16; o >= 1; o >>= 1) Sd += __shfl_xor_sync(FULL_MASK, Sd, o);
   if (lane == 0) s_red[warp] = Sd;
@@ -579,12 +587,14 @@ __global__ void __launch_bounds__(FUSED_THREADS) k_fusedk(const IterParams Q, in
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x < 2 * KMAX - 1) s_w[threadIdx.x] = Q.tab.w[threadIdx.x];
   for (int e = threadIdx.x; e < TILE * K; e += FUSED_THREADS) (&s_colh[0][0])[e] = 0.f;
+  __shared__ int s_ij[2];
   double Sd = 0.0;
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    int I, J;
-    tile_decode(t, Q.tiles, I, J);
-    const int64_t i0 = (int64_t)I * TILE, j0 = (int64_t)J * TILE;
     __syncthreads();
+    if (threadIdx.x == 0) tile_decode(t, Q.tiles, s_ij[0], s_ij[1]);
+    __syncthreads();
+    const int I = s_ij[0], J = s_ij[1];
+    const int64_t i0 = (int64_t)I * TILE, j0 = (int64_t)J * TILE;
     for (int e = threadIdx.x; e < 2 * TILE; e += FUSED_THREADS) {
       const int side = e / TILE, l = e % TILE;
       int64_t g = (side ? j0 : i0) + l;
