@@ -325,8 +325,10 @@ def _plain_and_variants(G, X, Y0, n, k, nu, T, stream, chosen_final, P):
              "iters_per_s_iteration_phase": round(1e3 / it, 1),
              "iters_per_s_whole_fit": round(T / ((b + it * (T + 1)) / 1e3), 3),
              "final_stress": f,
+             "chosen_final_stress": chosen_final,
              "chosen_vs_plain_final_stress_rel_diff": abs(chosen_final - f) / f,
-             "equal_final_stress_1e-4": abs(chosen_final - f) / f <= 1e-4}
+             "equal_final_stress_1e-4": abs(chosen_final - f) / f <= 1e-4,
+             "chosen_not_worse_1e-4": chosen_final <= f * (1 + 1e-4)}
     variants = {}
     for name, (dt, pol) in FORMS.items():
         Dv = G.gini_pack(D, dt)
@@ -345,6 +347,7 @@ def _plain_and_variants(G, X, Y0, n, k, nu, T, stream, chosen_final, P):
                           "achieved_gbs": round(P * bpp / (itv / 1e3) / 1e9, 1),
                           "final_stress": float(fv),
                           "final_stress_rel_diff_vs_plain": abs(float(fv) - f) / f,
+                          "not_worse_than_plain_1e-4": float(fv) <= f * (1 + 1e-4),
                           "speedup_vs_plain": round(it / itv, 3)}
         del Dv
     del mats, D
