@@ -225,6 +225,45 @@ typedef struct {
  * fused stress+adjoint kernel, FULL the plain forward + adjoint kernels. */
 int gini_mds_fit(const gini_fit_args* args, void* ws, size_t ws_bytes, void* stream);
 
+/* One data set of a batched fit. */
+typedef struct {
+  const float* X_dev;  /* [n][ldx] float data */
+  int64_t n;           /* points, 2 .. 524,280 */
+  int64_t p;           /* features, 1 .. 1024 */
+  int64_t ldx;         /* >= p */
+} gini_problem;
+
+/* Bytes of workspace gini_fit_batched needs for these problems. */
+size_t gini_batch_workspace_size(const gini_problem* probs, int nprob, int n_nu, int restarts,
+                                 int iters);
+
+/* Many k = 2 fits at once: every problem x every nu of the grid x `restarts`
+ * starting points (the loops of Algorithm 1 over nu and starts).  For each
+ * problem one gini_dist call builds Delta for the whole grid (one sort per
+ * pair); then each iteration of all fits is one launch of a persistent kernel
+ * over every (problem, nu) tile, evaluating all restarts of a tile against one
+ * read of its dissimilarities; the T iterations, the final stress pass and the
+ * finalisation are captured once into a CUDA graph (kept for later calls with
+ * the same arguments) and launched on `stream`.  The kernel's row-block shape
+ * and CTAs per SM are chosen by timing the candidates on this batch at its
+ * first call (cached per batch shape).  Each fit runs gini_mds_fit's iteration
+ * with eta = gini_default_step(n, 2, nu, sum_delta2, eta0).
+ *   nu_host      n_nu values (1..8), each > 1
+ *   restarts     1..16
+ *   Y0_dev       starting points, problem-major: problem q holds restarts x n_q x 2
+ *                floats (the same starts serve every nu)
+ *   Y_dev        out, (problem, nu, restart)-major: restarts x n_q x 2 floats per
+ *                (q, nu)
+ *   history_dev  (iters + 1) x nfits doubles out (S after t iterations), or NULL;
+ *                fits are ordered (problem, nu, restart)
+ *   final_stress_dev  nfits doubles out, S(Y_T)
+ *   tuned_config out (host), or NULL: 100 x rows-per-warp + CTAs per SM chosen
+ * Non-finite data are reported by gini_check(ws, stream). */
+int gini_fit_batched(const gini_problem* probs, int nprob, const double* nu_host, int n_nu,
+                     int restarts, int iters, double eta0, const float* Y0_dev, float* Y_dev,
+                     double* history_dev, double* final_stress_dev, int* tuned_config, void* ws,
+                     size_t ws_bytes, void* stream);
+
 /* A step size for gini_mds_fit: eta0 times the inverse of a Gershgorin bound
  * on the Gauss-Newton curvature of S,
  *   eta = eta0 * sum_delta2 / (2 (n-1) k ((k/2) w_max)^2),  w_max = ((k-1)/k)^{nu-1}.

@@ -21,6 +21,11 @@ _vp = _c.c_void_p
 _i64 = _c.c_int64
 
 
+class Problem(_c.Structure):
+    """Mirror of gini_problem in include/gini_mds.h."""
+    _fields_ = [("X_dev", _vp), ("n", _i64), ("p", _i64), ("ldx", _i64)]
+
+
 class FitArgs(_c.Structure):
     """Mirror of gini_fit_args in include/gini_mds.h."""
     _fields_ = [
@@ -52,6 +57,11 @@ SIGNATURES = {
     "gini_stress_grad_noalloc": (_c.c_int, [_vp, _i64, _c.c_int, _c.c_double, _vp, _c.c_int,
                                             _c.c_int, _i64, _vp, _c.c_double, _vp, _vp, _vp]),
     "gini_default_step": (_c.c_double, [_i64, _c.c_int, _c.c_double, _c.c_double, _c.c_double]),
+    "gini_batch_workspace_size": (_c.c_size_t, [_c.POINTER(Problem), _c.c_int, _c.c_int,
+                                                _c.c_int, _c.c_int]),
+    "gini_fit_batched": (_c.c_int, [_c.POINTER(Problem), _c.c_int, _c.POINTER(_c.c_double),
+                                    _c.c_int, _c.c_int, _c.c_int, _c.c_double, _vp, _vp, _vp,
+                                    _vp, _c.POINTER(_c.c_int), _vp, _c.c_size_t, _vp]),
 }
 
 _lib = None

@@ -201,6 +201,49 @@ def gini_mds_fit(Y0: torch.Tensor, nu: float, D: Dissimilarity, eta: float, iter
     return Y, hist, final
 
 
+def gini_fit_batched(Xs, nus, restarts: int, iters: int, Y0: torch.Tensor, eta0: float = 1.0,
+                     history: bool = False, ws: Optional[Workspace] = None,
+                     check_errors: bool = True):
+    """Batched k = 2 fits of every problem x nu x restart.
+
+    Xs: list of (n_q, p_q) float32 CUDA tensors.  Y0: flat float32 tensor,
+    problem-major, restarts x n_q x 2 per problem.  Returns a dict with
+    "Y" (flat, (problem, nu, restart)-major), "final" ((nprob, n_nu,
+    restarts) float64), "history" ((iters+1, nprob, n_nu, restarts) or None)
+    and "tuned" (100 x rows per warp + CTAs per SM chosen by the autotuner).
+    """
+    nus = [float(v) for v in nus]
+    nprob, n_nu = len(Xs), len(nus)
+    probs = (_lib.Problem * nprob)()
+    keep = []
+    for q, X in enumerate(Xs):
+        _require_cuda(X)
+        assert X.dtype == torch.float32 and X.dim() == 2 and X.stride(1) == 1
+        keep.append(X)
+        probs[q] = _lib.Problem(X.data_ptr(), X.shape[0], X.shape[1], X.stride(0))
+    ns = [X.shape[0] for X in Xs]
+    assert Y0.numel() == sum(restarts * n * 2 for n in ns)
+    dev = Xs[0].device
+    Y = torch.empty(sum(n_nu * restarts * n * 2 for n in ns), dtype=torch.float32, device=dev)
+    nfits = nprob * n_nu * restarts
+    final = torch.empty(nfits, dtype=torch.float64, device=dev)
+    hist = torch.empty((iters + 1) * nfits, dtype=torch.float64, device=dev) if history else None
+    nbytes = int(lib().gini_batch_workspace_size(probs, nprob, n_nu, restarts, iters))
+    ws = ws or workspace(dev)
+    buf = ws.ensure(nbytes)
+    nu_arr = (ctypes.c_double * n_nu)(*nus)
+    tuned = ctypes.c_int(0)
+    st = lib().gini_fit_batched(probs, nprob, nu_arr, n_nu, restarts, iters, float(eta0),
+                                _ptr(Y0.contiguous()), _ptr(Y), _ptr(hist), _ptr(final),
+                                ctypes.byref(tuned), _ptr(buf), buf.numel(), _stream())
+    check(st, "gini_fit_batched")
+    if check_errors:
+        ws.check()
+    return {"Y": Y, "final": final.view(nprob, n_nu, restarts),
+            "history": hist.view(iters + 1, nprob, n_nu, restarts) if hist is not None else None,
+            "tuned": tuned.value}
+
+
 class GiniStress(torch.autograd.Function):
     """S(Y) = sum_{i<j} (Dbar(y_i, y_j) - delta_ij)^2 / sum_delta2 as an autograd op.
 

@@ -1,0 +1,91 @@
+"""gini_fit_batched (many problems x nu grid x restarts in one graph) against
+independent single fits on the GPU and against the FP64 oracle."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import gini_oracle as orc
+from paper_2605_25124_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+def _batch(seed, ns, ps, restarts):
+    Xs = [wl.gaussian_outliers(n, p, seed=seed + q) for q, (n, p) in enumerate(zip(ns, ps))]
+    Y0s = [wl.y_init(restarts * n, 2, seed=seed + 100 + q, sd=1.0) for q, n in enumerate(ns)]
+    return Xs, Y0s
+
+
+def _slices(ns, n_nu, R):
+    """Offsets of fit (q, v, r) in the batched Y output."""
+    off, out = 0, {}
+    for q, n in enumerate(ns):
+        for v in range(n_nu):
+            for r in range(R):
+                out[q, v, r] = (off, off + 2 * n)
+                off += 2 * n
+    return out
+
+
+def test_batched_matches_single_fits(G):
+    ns, ps, nus, R, T = [150, 300, 77], [5, 12, 30], [1.5, 2.0, 3.0], 3, 20
+    Xs, Y0s = _batch(500, ns, ps, R)
+    Xd = [torch.from_numpy(X).cuda() for X in Xs]
+    Y0 = torch.from_numpy(np.concatenate([y.reshape(-1) for y in Y0s])).cuda()
+    out = G.gini_fit_batched(Xd, nus, R, T, Y0, eta0=1.0, history=True)
+    Yb = out["Y"].cpu().numpy()
+    sl = _slices(ns, len(nus), R)
+    for q, n in enumerate(ns):
+        mats, _ = G.gini_dist(Xd[q], nus, layout="full")
+        for v, nu in enumerate(nus):
+            D = G.gini_pack(mats[v], "f32")
+            eta = G.default_step(n, 2, nu, D.sum_delta2, 1.0)
+            for r in range(R):
+                y0 = torch.from_numpy(Y0s[q][r * n:(r + 1) * n]).cuda()
+                Ys, hs, fs = G.gini_mds_fit(y0, nu, D, eta, T)
+                h = out["history"][:, q, v, r].cpu().numpy()
+                hr = hs.cpu().numpy()
+                assert np.max(np.abs(h - hr) / hr) <= 1e-4, (q, v, r)
+                a, b = sl[q, v, r]
+                Yq = Yb[a:b].reshape(n, 2)
+                assert np.max(np.abs(Yq - Ys.cpu().numpy())) <= 1e-4 * np.abs(Yq).max()
+                assert out["final"][q, v, r].item() == pytest.approx(float(fs), rel=1e-4)
+    assert out["tuned"] in (1601, 1602, 1603, 801, 802)
+
+
+def test_batched_one_step_against_oracle(G):
+    ns, ps, nus, R = [130, 260], [7, 9], [1.3, 2.5], 2
+    Xs, Y0s = _batch(600, ns, ps, R)
+    Xd = [torch.from_numpy(X).cuda() for X in Xs]
+    Y0 = torch.from_numpy(np.concatenate([y.reshape(-1) for y in Y0s])).cuda()
+    out = G.gini_fit_batched(Xd, nus, R, 1, Y0, eta0=0.5, history=True)
+    Yb = out["Y"].cpu().numpy()
+    sl = _slices(ns, len(nus), R)
+    for q, n in enumerate(ns):
+        D, sd2 = orc.delta(Xs[q], nus)
+        for v, nu in enumerate(nus):
+            eta = G.default_step(n, 2, nu, sd2[v], 0.5)
+            for r in range(R):
+                y0 = Y0s[q][r * n:(r + 1) * n].astype(np.float64)
+                y1, h = orc.fit(D[v], nu, sd2[v], y0, eta, 1)
+                assert out["history"][0, q, v, r].item() == pytest.approx(h[0], rel=1e-5)
+                a, b = sl[q, v, r]
+                step = Yb[a:b].reshape(n, 2) - y0
+                step_ref = y1 - y0
+                assert np.max(np.abs(step - step_ref)) <= (1e-5 * np.abs(step_ref).max()
+                                                          + 2e-7 * np.abs(y0).max())
+
+
+def test_batched_graph_reuse_and_errors(G):
+    from paper_2605_25124_gb300._lib import GiniError
+    ns, ps, nus, R, T = [200, 90], [6, 4], [2.0], 2, 10
+    Xs, Y0s = _batch(700, ns, ps, R)
+    Xd = [torch.from_numpy(X).cuda() for X in Xs]
+    Y0 = torch.from_numpy(np.concatenate([y.reshape(-1) for y in Y0s])).cuda()
+    a = G.gini_fit_batched(Xd, nus, R, T, Y0)
+    b = G.gini_fit_batched(Xd, nus, R, T, Y0)  # replays the cached graph from Y0
+    np.testing.assert_allclose(a["final"].cpu().numpy(), b["final"].cpu().numpy(), rtol=1e-5)
+    with pytest.raises(GiniError, match="EINVAL"):
+        G.gini_fit_batched(Xd, nus, 17, T, torch.zeros(17 * 290 * 2, device="cuda"))
+    with pytest.raises(GiniError, match="EINVAL"):
+        G.gini_fit_batched(Xd, [0.9], R, T, Y0)
