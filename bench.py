@@ -240,12 +240,13 @@ def run_ours(args, rank, local, world):
     b_s = statistics.mean(build_ms) / 1e3
     build_tflops = 3.0 * p * P / b_s / 1e12
     ranked_per_s = P * p / b_s
-    # ALU roofline of the sort: comparison lower bound p ceil(log2 p) per pair
-    # plus the 3p useful flops, against one op per FP32 lane per clock.
-    ops_per_pair = p * math.ceil(math.log2(p)) + 3 * p
+    # ALU roofline of the sort: the comparison lower bound p ceil(log2 p) per
+    # pair against the ALU pipe's rate (min/max/compare execute there: 64 lanes
+    # per SM per clock on this part, half the FP32 FMA rate).
+    ops_per_pair = p * math.ceil(math.log2(p))
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     max_mhz = clocks.get("sm_max_mhz") or 2070.0
-    alu_peak = sms * 128 * max_mhz * 1e6
+    alu_peak = sms * 64 * max_mhz * 1e6
     achieved_ops = P * ops_per_pair / b_s
     traffic = _profile_traffic()
 
@@ -277,8 +278,8 @@ def run_ours(args, rank, local, world):
                      "peak": round(alu_peak / 1e12, 3), "unit": "Tops/s",
                      "frac": round(achieved_ops / alu_peak, 4),
                      "traffic": traffic.get("k_dist_bytes_per_launch"),
-                     "peak_note": f"{sms} SMs x 128 FP32 lanes x {max_mhz:.0f} MHz",
-                     "work_note": "per pair p*ceil(log2 p) compares + 3p flops"},
+                     "peak_note": f"ALU pipe: {sms} SMs x 64 lanes x {max_mhz:.0f} MHz",
+                     "work_note": "per pair p*ceil(log2 p) comparisons (sorting lower bound)"},
         "iter_roofline": {"kernel": "k_fused2 (+ k_update) per iteration", "bound": "hbm",
                           "achieved": round(iter_gbs, 1), "peak": hbm_peak, "unit": "GB/s",
                           "frac": round(iter_gbs / hbm_peak, 4), "peak_source": peak_src,
