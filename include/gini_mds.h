@@ -73,6 +73,21 @@ typedef enum {
   GINI_LAYOUT_TILED = 1
 } gini_layout;
 
+/* Distance measured between embedded points. */
+typedef enum {
+  GINI_METRIC_GINI = 0,   /* Dbar_{G,nu} in k dimensions (the default) */
+  GINI_METRIC_EUCLID = 1  /* ||y_i - y_j||_2, as in Algorithm 1's Kruskal stress line */
+} gini_metric;
+
+/* Loss between embedding distances d_ij and dissimilarities delta_ij. */
+typedef enum {
+  /* S = sum_{i<j} (d - delta)^2 / norm, norm = sum_{i<j} delta^2 (Kruskal) */
+  GINI_LOSS_KRUSKAL = 0,
+  /* S = sum_{i<j, delta > 0} (d - delta)^2 / delta / norm, norm = sum_{i<j} delta
+   * (Sammon, Section IV-B; the objective of Algorithm 2) */
+  GINI_LOSS_SAMMON = 1
+} gini_loss;
+
 /* Workspace queries (see gini_workspace_size). */
 typedef enum {
   GINI_OP_RANK = 0,
@@ -198,6 +213,22 @@ int gini_stress_grad_noalloc(const float* Y_dev, int64_t n, int k, double nu,
                              const float* col_scale_dev, double sum_delta2, double* stress_dev,
                              float* grad_dev, void* stream);
 
+/* gini_stress_grad for any metric and loss.  `norm` is the loss's
+ * normaliser (sum_{i<j} delta^2 for Kruskal, sum_{i<j} delta for Sammon; see
+ * gini_delta_sums), > 0.  dd/dy is (k/2) W(midrank) for the Gini metric and
+ * (y_i - y_j)/d (0 at d = 0) for the Euclidean one.  Same layouts, storage
+ * types, workspace and errors as gini_stress_grad (which is the Gini/Kruskal
+ * case of this function). */
+int gini_stress_grad_ex(const float* Y_dev, int64_t n, int k, double nu, const void* delta_dev,
+                        int layout, int dtype, int64_t ldd, const float* col_scale_dev,
+                        int metric, int loss, double norm, double* stress_dev, float* grad_dev,
+                        void* ws, size_t ws_bytes, void* stream);
+
+/* sums_dev[0] = sum_{i<j} delta_ij and sums_dev[1] = sum_{i<j} delta_ij^2 (FP64)
+ * of a stored dissimilarity matrix (any layout and storage type). */
+int gini_delta_sums(const void* delta_dev, int64_t n, int layout, int dtype, int64_t ldd,
+                    const float* col_scale_dev, double* sums_dev, void* stream);
+
 /* Arguments of gini_mds_fit. */
 typedef struct {
   int64_t n;                  /* points, >= 2 */
@@ -217,6 +248,9 @@ typedef struct {
   float* Y_dev;               /* [n][k] in: Y_0, out: Y_T */
   double* history_dev;        /* iters + 1 doubles out, S(Y_t) for t = 0..T, or NULL */
   double* final_stress_dev;   /* 1 double out, S(Y_T), or NULL */
+  int metric;                 /* gini_metric (0: Gini) */
+  int loss;                   /* gini_loss (0: Kruskal); sum_delta2 then holds the loss's
+                                 normaliser (sum delta^2, or sum delta for Sammon) */
 } gini_fit_args;
 
 /* T iterations of Y_{t+1} = Y_t - eta * dS/dY(Y_t) (the "Run MDS" step of

@@ -339,3 +339,56 @@ void orc_fit(const double* Delta, int64_t n, int k, double nu, double sum_delta2
   if (history) history[T] = S;
   free(g);
 }
+
+/* ------------------------------------------------------------------------- *
+ * Embedding losses beyond Kruskal stress with Gini distances.
+ *   metric 0: d_ij = Dbar_{G,nu}(y_i, y_j)      (as above)
+ *   metric 1: d_ij = ||y_i - y_j||_2            (Euclidean, Algorithm 1's KS line)
+ *   loss 0 (Kruskal): S = sum_{i<j} (d_ij - delta_ij)^2 / norm, norm = sum delta^2
+ *   loss 1 (Sammon):  S = sum_{i<j, delta_ij > 0} (d_ij - delta_ij)^2 / delta_ij / norm,
+ *                     norm = sum_{i<j} delta_ij  (Section IV-B, Sammon loss)
+ * grad[i] = dS/dy_i by a double loop over ordered pairs; the Euclidean
+ * derivative (y_i - y_j)/d_ij is taken as 0 at d_ij = 0.
+ * ------------------------------------------------------------------------- */
+static double euclid_grad(const double* x, const double* y, int k, double* dz) {
+  double s = 0.0;
+  for (int c = 0; c < k; ++c) s += (x[c] - y[c]) * (x[c] - y[c]);
+  double d = sqrt(s);
+  if (dz)
+    for (int c = 0; c < k; ++c) dz[c] = d > 0.0 ? (x[c] - y[c]) / d : 0.0;
+  return d;
+}
+
+double orc_stress_grad_ex(const double* Y, int64_t n, int k, double nu, const double* Delta,
+                          int64_t ldd, int metric, int loss, double norm, double* grad) {
+  double S = 0.0;
+#pragma omp parallel reduction(+ : S)
+  {
+    orc_work w;
+    work_alloc(&w, k);
+#pragma omp for schedule(dynamic, 4)
+    for (int64_t i = 0; i < n; ++i) {
+      if (grad) for (int c = 0; c < k; ++c) grad[i * k + c] = 0.0;
+      for (int64_t j = 0; j < n; ++j) {
+        if (j == i) continue;
+        const double* yi = Y + i * k;
+        const double* yj = Y + j * k;
+        double dij = metric == 1 ? euclid_grad(yi, yj, k, grad ? w.dz : NULL)
+                                 : pd_work(yi, yj, k, nu, grad ? w.dz : NULL, w.zf, w.zb, w.rf,
+                                           w.rb);
+        double delta = Delta[i * ldd + j];
+        double r = dij - delta;
+        double wgt = 1.0;
+        if (loss == 1) {
+          if (!(delta > 0.0)) continue;
+          wgt = 1.0 / delta;
+        }
+        if (j > i) S += wgt * r * r;
+        if (grad)
+          for (int c = 0; c < k; ++c) grad[i * k + c] += 2.0 * wgt * r / norm * w.dz[c];
+      }
+    }
+    work_free(&w);
+  }
+  return S / norm;
+}

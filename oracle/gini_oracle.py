@@ -62,6 +62,10 @@ def lib():
                                     _I64P, _I64, ctypes.c_double, _F64P]
         L.orc_fit.argtypes = [_F64P, _I64, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                               ctypes.c_double, ctypes.c_int, _F64P, _F64P]
+        L.orc_stress_grad_ex.argtypes = [_F64P, _I64, ctypes.c_int, ctypes.c_double, _F64P,
+                                         _I64, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                         _F64P]
+        L.orc_stress_grad_ex.restype = ctypes.c_double
         L.orc_set_threads.argtypes = [ctypes.c_int]
         L.orc_get_threads.restype = ctypes.c_int
         _lib = L
@@ -187,3 +191,20 @@ def fit(Delta, nu, sum_delta2, Y0, eta, T):
     lib().orc_fit(_p(Delta, _F64P), n, k, float(nu), float(sum_delta2), float(eta), int(T),
                   _p(Y, _F64P), _p(h, _F64P))
     return Y, h
+
+
+METRICS = {"gini": 0, "euclid": 1}
+LOSSES = {"kruskal": 0, "sammon": 1}
+
+
+def stress_grad_ex(Y, nu, Delta, norm, metric="gini", loss="kruskal", grad: bool = True):
+    """(S, dS/dY or None) for metric "gini"/"euclid" and loss "kruskal"/"sammon";
+    norm = sum delta^2 (Kruskal) or sum delta (Sammon) over i<j."""
+    Y = _f64(Y)
+    Delta = _f64(Delta)
+    n, k = Y.shape
+    g = np.empty((n, k), dtype=np.float64) if grad else None
+    S = lib().orc_stress_grad_ex(_p(Y, _F64P), n, k, float(nu), _p(Delta, _F64P),
+                                 Delta.shape[1], METRICS[metric], LOSSES[loss], float(norm),
+                                 _p(g, _F64P) if grad else None)
+    return float(S), g

@@ -13,6 +13,8 @@ LIB_PATH = os.path.join(_HERE, "_build", "libginimds.so")
 
 GINI_OK, GINI_EINVAL, GINI_ENONFINITE, GINI_EDEGENERATE, GINI_ENOMEM, GINI_ECUDA, GINI_ETIMEOUT = range(7)
 DTYPES = {"f32": 0, "bf16": 1, "bf16x2": 2, "fp8": 3}
+METRICS = {"gini": 0, "euclid": 1}
+LOSSES = {"kruskal": 0, "sammon": 1}
 LAYOUTS = {"full": 0, "tiled": 1}
 OPS = {"rank": 0, "dist": 1, "stress": 2, "fit": 3}
 
@@ -33,7 +35,8 @@ class FitArgs(_c.Structure):
         ("delta_dev", _vp), ("layout", _c.c_int), ("dtype", _c.c_int), ("ldd", _i64),
         ("col_scale_dev", _vp), ("sum_delta2", _c.c_double), ("eta", _c.c_double),
         ("iters", _c.c_int), ("polish_iters", _c.c_int), ("Y_dev", _vp),
-        ("history_dev", _vp), ("final_stress_dev", _vp),
+        ("history_dev", _vp), ("final_stress_dev", _vp), ("metric", _c.c_int),
+        ("loss", _c.c_int),
     ]
 
 
@@ -54,6 +57,10 @@ SIGNATURES = {
     "gini_stress_grad": (_c.c_int, [_vp, _i64, _c.c_int, _c.c_double, _vp, _c.c_int, _c.c_int,
                                     _i64, _vp, _c.c_double, _vp, _vp, _vp, _c.c_size_t, _vp]),
     "gini_mds_fit": (_c.c_int, [_c.POINTER(FitArgs), _vp, _c.c_size_t, _vp]),
+    "gini_stress_grad_ex": (_c.c_int, [_vp, _i64, _c.c_int, _c.c_double, _vp, _c.c_int,
+                                       _c.c_int, _i64, _vp, _c.c_int, _c.c_int, _c.c_double,
+                                       _vp, _vp, _vp, _c.c_size_t, _vp]),
+    "gini_delta_sums": (_c.c_int, [_vp, _i64, _c.c_int, _c.c_int, _i64, _vp, _vp, _vp]),
     "gini_stress_grad_noalloc": (_c.c_int, [_vp, _i64, _c.c_int, _c.c_double, _vp, _c.c_int,
                                             _c.c_int, _i64, _vp, _c.c_double, _vp, _vp, _vp]),
     "gini_default_step": (_c.c_double, [_i64, _c.c_int, _c.c_double, _c.c_double, _c.c_double]),

@@ -13,7 +13,7 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import DTYPES, LAYOUTS, OPS, check, lib
+from ._lib import DTYPES, LAYOUTS, LOSSES, METRICS, OPS, check, lib
 
 
 def _ptr(t: Optional[torch.Tensor]):
@@ -155,9 +155,21 @@ def gini_pack(D: Dissimilarity, dtype: str) -> Dissimilarity:
     return Dissimilarity(out, n, "tiled", dtype, D.sum_delta2, scale)
 
 
+def gini_delta_sums(D: Dissimilarity):
+    """(sum_{i<j} delta, sum_{i<j} delta^2) of a stored matrix, as a float64
+    tensor of 2 on the device."""
+    out = torch.empty(2, dtype=torch.float64, device=D.data.device)
+    st = lib().gini_delta_sums(_ptr(D.data), D.n, LAYOUTS[D.layout], DTYPES[D.dtype], D.ldd,
+                               _ptr(D.col_scale), _ptr(out), _stream())
+    check(st, "gini_delta_sums")
+    return out
+
+
 def gini_stress_grad(Y: torch.Tensor, nu: float, D: Dissimilarity, grad: bool = True,
-                     ws: Optional[Workspace] = None, check_errors: bool = True):
-    """(S as a float64 0-d tensor, dS/dY or None)."""
+                     ws: Optional[Workspace] = None, check_errors: bool = True,
+                     metric: str = "gini", loss: str = "kruskal", norm: Optional[float] = None):
+    """(S as a float64 0-d tensor, dS/dY or None).  norm defaults to
+    D.sum_delta2 (the Kruskal normaliser); Sammon needs sum_{i<j} delta."""
     _require_cuda(Y)
     assert Y.dtype == torch.float32 and Y.is_contiguous()
     n, k = Y.shape
@@ -165,9 +177,11 @@ def gini_stress_grad(Y: torch.Tensor, nu: float, D: Dissimilarity, grad: bool = 
     g = torch.empty_like(Y) if grad else None
     ws = ws or workspace(Y.device)
     buf = ws.ensure(workspace_size("stress", n, 0, k))
-    st = lib().gini_stress_grad(_ptr(Y), n, k, float(nu), _ptr(D.data), LAYOUTS[D.layout],
-                                DTYPES[D.dtype], D.ldd, _ptr(D.col_scale), D.sum_delta2,
-                                _ptr(stress), _ptr(g), _ptr(buf), buf.numel(), _stream())
+    nrm = D.sum_delta2 if norm is None else float(norm)
+    st = lib().gini_stress_grad_ex(_ptr(Y), n, k, float(nu), _ptr(D.data), LAYOUTS[D.layout],
+                                   DTYPES[D.dtype], D.ldd, _ptr(D.col_scale), METRICS[metric],
+                                   LOSSES[loss], nrm, _ptr(stress), _ptr(g), _ptr(buf),
+                                   buf.numel(), _stream())
     check(st, "gini_stress_grad")
     if check_errors:
         ws.check()
@@ -176,7 +190,8 @@ def gini_stress_grad(Y: torch.Tensor, nu: float, D: Dissimilarity, grad: bool = 
 
 def gini_mds_fit(Y0: torch.Tensor, nu: float, D: Dissimilarity, eta: float, iters: int,
                  polish_iters: int = 0, history: bool = True, ws: Optional[Workspace] = None,
-                 check_errors: bool = True, out: Optional[torch.Tensor] = None):
+                 check_errors: bool = True, out: Optional[torch.Tensor] = None,
+                 metric: str = "gini", loss: str = "kruskal", norm: Optional[float] = None):
     """Fixed-step GD on the normalized stress; returns (Y_T, history or None, S(Y_T))."""
     _require_cuda(Y0)
     n, k = Y0.shape
@@ -190,7 +205,9 @@ def gini_mds_fit(Y0: torch.Tensor, nu: float, D: Dissimilarity, eta: float, iter
     a = _lib.FitArgs(n=n, k=k, nu=float(nu), delta_dev=D.data.data_ptr(),
                      layout=LAYOUTS[D.layout], dtype=DTYPES[D.dtype], ldd=D.ldd,
                      col_scale_dev=(D.col_scale.data_ptr() if D.col_scale is not None else None),
-                     sum_delta2=D.sum_delta2, eta=float(eta), iters=int(iters),
+                     sum_delta2=(D.sum_delta2 if norm is None else float(norm)),
+                     eta=float(eta), iters=int(iters), metric=METRICS[metric],
+                     loss=LOSSES[loss],
                      polish_iters=int(polish_iters), Y_dev=Y.data_ptr(),
                      history_dev=(hist.data_ptr() if hist is not None else None),
                      final_stress_dev=final.data_ptr())

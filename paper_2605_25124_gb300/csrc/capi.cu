@@ -167,3 +167,106 @@ extern "C" int gini_pack(const float* delta_full_dev, int64_t n, int64_t ldd, in
   if (e != cudaSuccess) { gini_set_cuda_error(e); return GINI_ECUDA; }
   return GINI_OK;
 }
+
+// ---------------------------------------------------------- delta sums ----
+
+// sum_{i<j} delta and delta^2 over a stored matrix; one thread per row of the
+// FULL layout or per stored tile element of the TILED one.
+template <int DT>
+__device__ __forceinline__ float tiled_value(const void* D, int64_t e, int64_t plane,
+                                             const float* scale, int64_t j) {
+  if (DT == GINI_F32) return reinterpret_cast<const float*>(D)[e];
+  if (DT == GINI_BF16) return __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(D)[e]);
+  if (DT == GINI_BF16X2)
+    return __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(D)[e]) +
+           __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(D)[plane + e]);
+  __half_raw hr = __nv_cvt_fp8_to_halfraw(reinterpret_cast<const __nv_fp8_storage_t*>(D)[e],
+                                          __NV_E4M3);
+  return __half2float(__half(hr)) * scale[j];
+}
+
+__device__ __forceinline__ void block_sums_add(double a, double b, double* out) {
+  __shared__ double s[2][8];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) {
+    a += __shfl_xor_sync(FULL_MASK, a, o);
+    b += __shfl_xor_sync(FULL_MASK, b, o);
+  }
+  if (lane == 0) {
+    s[0][warp] = a;
+    s[1][warp] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double x = 0.0, y = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      x += s[0][w];
+      y += s[1][w];
+    }
+    atomicAdd(out, x);
+    atomicAdd(out + 1, y);
+  }
+}
+
+__global__ void k_sums_full(const float* __restrict__ D, int64_t n, int64_t ldd, double* out) {
+  double a = 0.0, b = 0.0;
+  for (int64_t i = blockIdx.x; i < n; i += gridDim.x)
+    for (int64_t j = i + 1 + threadIdx.x; j < n; j += blockDim.x) {
+      const double v = D[i * ldd + j];
+      a += v;
+      b += v * v;
+    }
+  block_sums_add(a, b, out);
+}
+
+template <int DT>
+__global__ void k_sums_tiled(const void* D, int64_t n, int64_t T, int64_t plane,
+                             const float* scale, double* out) {
+  __shared__ int s_ij[2];
+  const int64_t t = blockIdx.x;
+  if (threadIdx.x == 0) tile_decode(t, T, s_ij[0], s_ij[1]);
+  __syncthreads();
+  double a = 0.0, b = 0.0;
+  for (int rc = threadIdx.x; rc < TILE * TILE; rc += blockDim.x) {
+    const int64_t i = (int64_t)s_ij[0] * TILE + rc / TILE, j = (int64_t)s_ij[1] * TILE + rc % TILE;
+    if (i < j && j < n) {
+      const double v = tiled_value<DT>(D, t * TILE * TILE + rc, plane, scale, j);
+      a += v;
+      b += v * v;
+    }
+  }
+  block_sums_add(a, b, out);
+}
+
+extern "C" int gini_delta_sums(const void* delta_dev, int64_t n, int layout, int dtype,
+                               int64_t ldd, const float* col_scale_dev, double* sums_dev,
+                               void* stream) {
+  if (!delta_dev || !sums_dev || n < 2 || n > ((int64_t)1 << 31)) return GINI_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaMemsetAsync(sums_dev, 0, 2 * sizeof(double), s);
+  if (e != cudaSuccess) { gini_set_cuda_error(e); return GINI_ECUDA; }
+  if (layout == GINI_LAYOUT_FULL) {
+    if (dtype != GINI_F32 || ldd < n) return GINI_EINVAL;
+    const unsigned g = (unsigned)(n < 4096 ? n : 4096);
+    gini_count_launch(1);
+    k_sums_full<<<g, 256, 0, s>>>((const float*)delta_dev, n, ldd, sums_dev);
+  } else if (layout == GINI_LAYOUT_TILED) {
+    if (dtype == GINI_FP8E4M3 && !col_scale_dev) return GINI_EINVAL;
+    const int64_t T = tiles_1d(n), plane = gini_tiled_elems(n);
+    const unsigned g = (unsigned)(T * (T + 1) / 2);
+    gini_count_launch(1);
+    switch (dtype) {
+      case GINI_F32: k_sums_tiled<GINI_F32><<<g, 256, 0, s>>>(delta_dev, n, T, plane, col_scale_dev, sums_dev); break;
+      case GINI_BF16: k_sums_tiled<GINI_BF16><<<g, 256, 0, s>>>(delta_dev, n, T, plane, col_scale_dev, sums_dev); break;
+      case GINI_BF16X2: k_sums_tiled<GINI_BF16X2><<<g, 256, 0, s>>>(delta_dev, n, T, plane, col_scale_dev, sums_dev); break;
+      case GINI_FP8E4M3: k_sums_tiled<GINI_FP8E4M3><<<g, 256, 0, s>>>(delta_dev, n, T, plane, col_scale_dev, sums_dev); break;
+      default: return GINI_EINVAL;
+    }
+  } else {
+    return GINI_EINVAL;
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) { gini_set_cuda_error(e); return GINI_ECUDA; }
+  return GINI_OK;
+}

@@ -48,7 +48,49 @@ struct IterParams {
   double* stress;    // FP64 accumulator of sum r^2
   PairTab tab;
   unsigned* err;
+  int metric;        // GINI_METRIC_GINI or GINI_METRIC_EUCLID
+  int loss;          // GINI_LOSS_KRUSKAL or GINI_LOSS_SAMMON
 };
+
+// Gini distance with Kruskal stress and k = 2 takes the scalar fast path
+// (one accumulator per point, the gradient is c2 h_i (1, -1)).
+__host__ __device__ __forceinline__ bool scalar2_path(int k, int metric, int loss) {
+  return k == 2 && metric == GINI_METRIC_GINI && loss == GINI_LOSS_KRUSKAL;
+}
+
+// Euclidean embedding distance ||y_i - y_j|| and its derivative in y_i
+// ((y_i - y_j)/d, taken as 0 at d = 0).
+template <int K>
+__device__ __forceinline__ float pair_euclid(const float* yi, const float* yj, float (&dw)[K]) {
+  float s = 0.f;
+#pragma unroll
+  for (int a = 0; a < K; ++a) {
+    dw[a] = yi[a] - yj[a];
+    s = fmaf(dw[a], dw[a], s);
+  }
+  const float d = sqrtf(s);
+  const float inv = d > 0.f ? 1.f / d : 0.f;
+#pragma unroll
+  for (int a = 0; a < K; ++a) dw[a] *= inv;
+  return d;
+}
+
+// Loss terms for one pair: stress term and gradient weight of dd/dy.
+//   Kruskal: (d - delta)^2 and (d - delta)
+//   Sammon:  (d - delta)^2 / delta and (d - delta) / delta, pairs with delta = 0
+//            excluded
+__device__ __forceinline__ void loss_terms(int loss, float d, float delta, float& sterm,
+                                           float& gw) {
+  const float r = d - delta;
+  if (loss == GINI_LOSS_SAMMON) {
+    const float w = delta > 0.f ? 1.f / delta : 0.f;
+    gw = r * w;
+    sterm = r * gw;
+  } else {
+    gw = r;
+    sterm = r * r;
+  }
+}
 
 // ------------------------------------------------------------ point prep ---
 
@@ -141,9 +183,10 @@ __global__ void __launch_bounds__(256) k_full(const IterParams Q) {
 #pragma unroll
     for (int c = 0; c < K; ++c) acc[c] = 0.f;
     float S = 0.f, Sc = 0.f;  // compensated FP32 sum over the row
+    const bool fast2 = scalar2_path(K, Q.metric, Q.loss);
     for (int64_t j = (FWD ? i + 1 : 0) + lane; j < Q.n; j += 32) {
       const float dl = __ldcs(D + i * Q.ldd + j);
-      if (K == 2) {
+      if (K == 2 && fast2) {
         float r, t;
         pair2(Pi[0], Q.P[j], Q.tab.c2, dl, r, t);
         if (FWD) {
@@ -156,20 +199,27 @@ __global__ void __launch_bounds__(256) k_full(const IterParams Q) {
         }
       } else {
         float yj[K], dw[K];
-        float2 Pj[NP];
 #pragma unroll
         for (int c = 0; c < K; ++c) yj[c] = Q.Y[j * K + c];
+        float d;
+        if (Q.metric == GINI_METRIC_EUCLID) {
+          d = pair_euclid<K>(yi, yj, dw);
+        } else {
+          float2 Pj[NP];
 #pragma unroll
-        for (int p = 0; p < NP; ++p) Pj[p] = Q.P[j * NP + p];
-        const float r = pair_k<K>(yi, yj, Pi, Pj, s_w, dw) - dl;
+          for (int p = 0; p < NP; ++p) Pj[p] = Q.P[j * NP + p];
+          d = pair_k<K>(yi, yj, Pi, Pj, s_w, dw);
+        }
+        float sterm, gw;
+        loss_terms(Q.loss, d, dl, sterm, gw);
         if (FWD) {
-          const float y = fmaf(r, r, -Sc);
+          const float y = sterm - Sc;
           const float tsum = S + y;
           Sc = (tsum - S) - y;
           S = tsum;
         } else if (j != i) {
 #pragma unroll
-          for (int c = 0; c < K; ++c) acc[c] = fmaf(r, dw[c], acc[c]);
+          for (int c = 0; c < K; ++c) acc[c] = fmaf(gw, dw[c], acc[c]);
         }
       }
     }
@@ -182,7 +232,7 @@ __global__ void __launch_bounds__(256) k_full(const IterParams Q) {
         for (int o = 16; o >= 1; o >>= 1) acc[c] += __shfl_xor_sync(FULL_MASK, acc[c], o);
       }
       if (lane == 0) {
-        if (K == 2) Q.h[i] = acc[0];
+        if (K == 2 && fast2) Q.h[i] = acc[0];
         else
 #pragma unroll
           for (int c = 0; c < K; ++c) Q.h[i * K + c] = acc[c];
@@ -631,12 +681,17 @@ __global__ void __launch_bounds__(FUSED_THREADS) k_fusedk(const IterParams Q, in
         const int cl = 4 * lane + c;
         const bool ok = gi < Q.n && j0 + cl < Q.n && (I != J || rl < cl);
         float dw[K];
-        float r = pair_k<K>(s_y[0][rl], s_y[1][cl], s_p[0][rl], s_p[1][cl], s_w, dw) - dl[c];
-        r = ok ? r : 0.f;
-        S = fmaf(r, r, S);
+        const float d = (Q.metric == GINI_METRIC_EUCLID)
+                            ? pair_euclid<K>(s_y[0][rl], s_y[1][cl], dw)
+                            : pair_k<K>(s_y[0][rl], s_y[1][cl], s_p[0][rl], s_p[1][cl], s_w, dw);
+        float sterm, gw;
+        loss_terms(Q.loss, d, dl[c], sterm, gw);
+        sterm = ok ? sterm : 0.f;
+        gw = ok ? gw : 0.f;
+        S += sterm;
 #pragma unroll
         for (int a = 0; a < K; ++a) {
-          const float tt = r * dw[a];
+          const float tt = gw * dw[a];
           racc[a] += tt;
           colacc[c][a] -= tt;
         }
@@ -677,7 +732,8 @@ __global__ void __launch_bounds__(FUSED_THREADS) k_fusedk(const IterParams Q, in
 // c2 * h_i * (1, -1)), then refresh the point pairs and clear h.
 template <int K>
 __global__ void k_update(float* __restrict__ Y, int64_t n, float2* __restrict__ P,
-                         float* __restrict__ h, float scale, float c2, unsigned* err) {
+                         float* __restrict__ h, float scale, float c2, bool scalar2,
+                         unsigned* err) {
   constexpr int NP = K * (K - 1) / 2;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   bool bad = false;
@@ -685,7 +741,7 @@ __global__ void k_update(float* __restrict__ Y, int64_t n, float2* __restrict__ 
     float y[K];
 #pragma unroll
     for (int c = 0; c < K; ++c) y[c] = Y[i * K + c];
-    if (K == 2) {
+    if (K == 2 && scalar2) {
       const float g = scale * c2 * h[i];
       y[0] -= g;
       y[1] += g;
@@ -712,10 +768,10 @@ __global__ void k_update(float* __restrict__ Y, int64_t n, float2* __restrict__ 
 }
 
 __global__ void k_finalize_grad(const float* __restrict__ h, int64_t n, int k, float scale,
-                                float c2, float* __restrict__ grad) {
+                                float c2, bool scalar2, float* __restrict__ grad) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  if (k == 2) {
+  if (k == 2 && scalar2) {
     const float g = scale * c2 * h[i];
     grad[i * 2] = g;
     grad[i * 2 + 1] = -g;
@@ -838,21 +894,21 @@ static void prep(int k, const float* Y, int64_t n, float2* P, unsigned* err, cud
 
 template <int K>
 static void launch_update(float* Y, int64_t n, float2* P, float* h, float scale, float c2,
-                          unsigned* err, cudaStream_t s) {
+                          bool scalar2, unsigned* err, cudaStream_t s) {
   gini_count_launch(1);
-  k_update<K><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(Y, n, P, h, scale, c2, err);
+  k_update<K><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(Y, n, P, h, scale, c2, scalar2, err);
 }
 
 static void update(int k, float* Y, int64_t n, float2* P, float* h, float scale, float c2,
-                   unsigned* err, cudaStream_t s) {
+                   bool scalar2, unsigned* err, cudaStream_t s) {
   switch (k) {
-    case 2: launch_update<2>(Y, n, P, h, scale, c2, err, s); break;
-    case 3: launch_update<3>(Y, n, P, h, scale, c2, err, s); break;
-    case 4: launch_update<4>(Y, n, P, h, scale, c2, err, s); break;
-    case 5: launch_update<5>(Y, n, P, h, scale, c2, err, s); break;
-    case 6: launch_update<6>(Y, n, P, h, scale, c2, err, s); break;
-    case 7: launch_update<7>(Y, n, P, h, scale, c2, err, s); break;
-    default: launch_update<8>(Y, n, P, h, scale, c2, err, s); break;
+    case 2: launch_update<2>(Y, n, P, h, scale, c2, scalar2, err, s); break;
+    case 3: launch_update<3>(Y, n, P, h, scale, c2, scalar2, err, s); break;
+    case 4: launch_update<4>(Y, n, P, h, scale, c2, scalar2, err, s); break;
+    case 5: launch_update<5>(Y, n, P, h, scale, c2, scalar2, err, s); break;
+    case 6: launch_update<6>(Y, n, P, h, scale, c2, scalar2, err, s); break;
+    case 7: launch_update<7>(Y, n, P, h, scale, c2, scalar2, err, s); break;
+    default: launch_update<8>(Y, n, P, h, scale, c2, scalar2, err, s); break;
   }
 }
 
@@ -892,6 +948,17 @@ static void launch_fused_dt(int k, const IterParams& Q, cudaStream_t s) {
   const int64_t ntiles = Q.tiles * (Q.tiles + 1) / 2;
   const int64_t cap = (int64_t)sm_count() * 4;
   const unsigned g = (unsigned)(ntiles < cap ? ntiles : cap);
+  if (!scalar2_path(k, Q.metric, Q.loss)) {
+    switch (k) {
+      case 2: launch_fusedk<2, DT, GRAD>(g, Q, ntiles, s); return;
+      case 3: launch_fusedk<3, DT, GRAD>(g, Q, ntiles, s); return;
+      case 4: launch_fusedk<4, DT, GRAD>(g, Q, ntiles, s); return;
+      case 5: launch_fusedk<5, DT, GRAD>(g, Q, ntiles, s); return;
+      case 6: launch_fusedk<6, DT, GRAD>(g, Q, ntiles, s); return;
+      case 7: launch_fusedk<7, DT, GRAD>(g, Q, ntiles, s); return;
+      default: launch_fusedk<8, DT, GRAD>(g, Q, ntiles, s); return;
+    }
+  }
   switch (k) {
     case 2: {
       using C = PipeCfg<DT>;
@@ -961,30 +1028,44 @@ static IterParams make_params(int64_t n, int k, double nu, const float* Y, const
   return Q;
 }
 
-extern "C" int gini_stress_grad(const float* Y_dev, int64_t n, int k, double nu,
-                                const void* delta_dev, int layout, int dtype, int64_t ldd,
-                                const float* col_scale_dev, double sum_delta2, double* stress_dev,
-                                float* grad_dev, void* ws, size_t ws_bytes, void* stream) {
+extern "C" int gini_stress_grad_ex(const float* Y_dev, int64_t n, int k, double nu,
+                                   const void* delta_dev, int layout, int dtype, int64_t ldd,
+                                   const float* col_scale_dev, int metric, int loss, double norm,
+                                   double* stress_dev, float* grad_dev, void* ws, size_t ws_bytes,
+                                   void* stream) {
   if (!Y_dev || !stress_dev || !ws) return GINI_EINVAL;
-  int st = check_common(n, k, nu, delta_dev, layout, dtype, ldd, col_scale_dev, sum_delta2);
+  if (metric != GINI_METRIC_GINI && metric != GINI_METRIC_EUCLID) return GINI_EINVAL;
+  if (loss != GINI_LOSS_KRUSKAL && loss != GINI_LOSS_SAMMON) return GINI_EINVAL;
+  int st = check_common(n, k, nu, delta_dev, layout, dtype, ldd, col_scale_dev, norm);
   if (st != GINI_OK) return st;
   if (ws_bytes < gini_workspace_size(GINI_OP_STRESS, n, 0, k, 0)) return GINI_ENOMEM;
   cudaStream_t s = (cudaStream_t)stream;
   IterWs w = carve(ws, n, k, 1);
   IterParams Q = make_params(n, k, nu, Y_dev, delta_dev, ldd, col_scale_dev, w);
+  Q.metric = metric;
+  Q.loss = loss;
   cudaError_t e = cudaMemsetAsync(w.acc, 0, sizeof(double), s);
   if (e == cudaSuccess && grad_dev) e = cudaMemsetAsync(w.h, 0, sizeof(float) * n * k, s);
   if (e != cudaSuccess) { gini_set_cuda_error(e); return GINI_ECUDA; }
   prep(k, Y_dev, n, w.P, w.err, s);
   one_pass(k, layout, dtype, grad_dev != nullptr, Q, s);
   gini_count_launch(grad_dev ? 2 : 1);
-  k_finalize_stress<<<1, 32, 0, s>>>(w.acc, 1, 1.0 / sum_delta2, nullptr, stress_dev);
+  k_finalize_stress<<<1, 32, 0, s>>>(w.acc, 1, 1.0 / norm, nullptr, stress_dev);
   if (grad_dev)
     k_finalize_grad<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
-        w.h, n, k, (float)(2.0 / sum_delta2), Q.tab.c2, grad_dev);
+        w.h, n, k, (float)(2.0 / norm), Q.tab.c2, scalar2_path(k, metric, loss), grad_dev);
   e = cudaGetLastError();
   if (e != cudaSuccess) { gini_set_cuda_error(e); return GINI_ECUDA; }
   return GINI_OK;
+}
+
+extern "C" int gini_stress_grad(const float* Y_dev, int64_t n, int k, double nu,
+                                const void* delta_dev, int layout, int dtype, int64_t ldd,
+                                const float* col_scale_dev, double sum_delta2, double* stress_dev,
+                                float* grad_dev, void* ws, size_t ws_bytes, void* stream) {
+  return gini_stress_grad_ex(Y_dev, n, k, nu, delta_dev, layout, dtype, ldd, col_scale_dev,
+                             GINI_METRIC_GINI, GINI_LOSS_KRUSKAL, sum_delta2, stress_dev,
+                             grad_dev, ws, ws_bytes, stream);
 }
 
 extern "C" int gini_mds_fit(const gini_fit_args* a, void* ws, size_t ws_bytes, void* stream) {
@@ -994,6 +1075,8 @@ extern "C" int gini_mds_fit(const gini_fit_args* a, void* ws, size_t ws_bytes, v
   if (st != GINI_OK) return st;
   if (a->iters < 0 || !(a->eta > 0.0) || !isfinite(a->eta) || a->polish_iters < 0)
     return GINI_EINVAL;
+  if (a->metric != GINI_METRIC_GINI && a->metric != GINI_METRIC_EUCLID) return GINI_EINVAL;
+  if (a->loss != GINI_LOSS_KRUSKAL && a->loss != GINI_LOSS_SAMMON) return GINI_EINVAL;
   if (ws_bytes < gini_workspace_size(GINI_OP_FIT, a->n, 0, a->k, a->iters)) return GINI_ENOMEM;
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t n = a->n;
@@ -1001,6 +1084,9 @@ extern "C" int gini_mds_fit(const gini_fit_args* a, void* ws, size_t ws_bytes, v
   const int T = a->iters;
   IterWs w = carve(ws, n, k, T + 1);
   IterParams Q = make_params(n, k, a->nu, a->Y_dev, a->delta_dev, a->ldd, a->col_scale_dev, w);
+  Q.metric = a->metric;
+  Q.loss = a->loss;
+  const bool sc2 = scalar2_path(k, a->metric, a->loss);
   cudaError_t e = cudaMemsetAsync(w.acc, 0, sizeof(double) * (size_t)(T + 1), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(w.h, 0, sizeof(float) * n * k, s);
   if (e != cudaSuccess) { gini_set_cuda_error(e); return GINI_ECUDA; }
@@ -1012,7 +1098,7 @@ extern "C" int gini_mds_fit(const gini_fit_args* a, void* ws, size_t ws_bytes, v
     if (dt == GINI_BF16X2 && a->layout == GINI_LAYOUT_TILED && t < polish_from) dt = GINI_BF16;
     Q.stress = w.acc + t;
     one_pass(k, a->layout, dt, true, Q, s);
-    update(k, a->Y_dev, n, w.P, w.h, scale, Q.tab.c2, w.err, s);
+    update(k, a->Y_dev, n, w.P, w.h, scale, Q.tab.c2, sc2, w.err, s);
   }
   Q.stress = w.acc + T;
   one_pass(k, a->layout, a->dtype, false, Q, s);
