@@ -298,6 +298,31 @@ int gini_fit_batched(const gini_problem* probs, int nprob, const double* nu_host
                      double* history_dev, double* final_stress_dev, int* tuned_config, void* ws,
                      size_t ws_bytes, void* stream);
 
+/* Bytes of workspace gini_classical_mds needs. */
+size_t gini_cmds_workspace_size(int64_t n, int k);
+
+/* Classical MDS of a dissimilarity matrix (Section IV-A): the top k
+ * eigenpairs of B = -1/2 H D2 H (D2 = elementwise squares of Delta,
+ * H = I - 11'/n) and the embedding Y = V_k Lambda_k^{1/2} (a negative
+ * eigenvalue gives a zero column).  B is not formed: block subspace iteration
+ * (16 columns, or n if fewer) streams Delta once per product -- `iters`
+ * products plus one for the final Rayleigh-Ritz step; after the first 5 the
+ * block iterates on B + s I, s the most negative Ritz value's magnitude, so
+ * the largest algebraic eigenvalues are found even where B has large negative
+ * ones.  A starting point for gini_mds_fit.
+ *   delta_dev    any layout / storage type (as gini_stress_grad)
+ *   k            1..8, <= n
+ *   iters        >= 1 (20 is ample for well separated eigenvalues)
+ *   seed         seeds the start block (SplitMix64 of seed + element index)
+ *   Y_dev        [n][k] float out
+ *   eigvals_dev  k doubles out, descending
+ * EINVAL on bad sizes, layouts or null pointers; ENOMEM when ws_bytes is short
+ * of gini_cmds_workspace_size.  Asynchronous on `stream`. */
+int gini_classical_mds(const void* delta_dev, int64_t n, int layout, int dtype, int64_t ldd,
+                       const float* col_scale_dev, int k, int iters, uint64_t seed,
+                       float* Y_dev, double* eigvals_dev, void* ws, size_t ws_bytes,
+                       void* stream);
+
 /* A step size for gini_mds_fit: eta0 times the inverse of a Gershgorin bound
  * on the Gauss-Newton curvature of S,
  *   eta = eta0 * sum_delta2 / (2 (n-1) k ((k/2) w_max)^2),  w_max = ((k-1)/k)^{nu-1}.

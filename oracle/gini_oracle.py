@@ -2,8 +2,9 @@
 
 TEST INFRASTRUCTURE ONLY: tests/, __graft_entry__.smoke() and the CPU-baseline
 / reference arm of bench.py are the only users.  The product path never imports
-this module.  Nothing here computes the method itself: every function forwards
-to the C oracle, whose header lists the paper passages each routine follows.
+this module.  Every function but classical_mds forwards to the C oracle, whose
+header lists the paper passages each routine follows; classical_mds is the
+textbook definition in numpy (its eigensolver a library step).
 """
 from __future__ import annotations
 
@@ -208,3 +209,18 @@ def stress_grad_ex(Y, nu, Delta, norm, metric="gini", loss="kruskal", grad: bool
                                  Delta.shape[1], METRICS[metric], LOSSES[loss], float(norm),
                                  _p(g, _F64P) if grad else None)
     return float(S), g
+
+
+def classical_mds(Delta, k: int):
+    """Classical MDS (Section IV-A) written as its definition: B = -1/2 H D2 H,
+    eigenpairs by numpy's symmetric eigensolver (a library step), the top k by
+    value, Y = V_k Lambda_k^{1/2} (negative eigenvalues give zero columns).
+    Returns (Y, eigenvalues descending)."""
+    D = np.asarray(Delta, dtype=np.float64)
+    n = D.shape[0]
+    H = np.eye(n) - np.full((n, n), 1.0 / n)
+    B = -0.5 * H @ (D * D) @ H
+    w, V = np.linalg.eigh(B)
+    idx = np.argsort(w)[::-1][:k]
+    lam = w[idx]
+    return V[:, idx] * np.sqrt(np.maximum(lam, 0.0)), lam

@@ -261,6 +261,25 @@ def gini_fit_batched(Xs, nus, restarts: int, iters: int, Y0: torch.Tensor, eta0:
             "tuned": tuned.value}
 
 
+def gini_classical_mds(D: Dissimilarity, k: int, iters: int = 20, seed: int = 0,
+                       ws: Optional[Workspace] = None, check_errors: bool = True):
+    """Classical MDS of D: (Y (n, k) float32, eigenvalues (k,) float64, descending)."""
+    n = D.n
+    dev = D.data.device
+    Y = torch.empty((n, k), dtype=torch.float32, device=dev)
+    lam = torch.empty(k, dtype=torch.float64, device=dev)
+    ws = ws or workspace(dev)
+    buf = ws.ensure(int(lib().gini_cmds_workspace_size(n, k)))
+    st = lib().gini_classical_mds(_ptr(D.data), n, LAYOUTS[D.layout], DTYPES[D.dtype], D.ldd,
+                                  _ptr(D.col_scale), int(k), int(iters),
+                                  int(seed) & 0xFFFFFFFFFFFFFFFF, _ptr(Y), _ptr(lam), _ptr(buf),
+                                  buf.numel(), _stream())
+    check(st, "gini_classical_mds")
+    if check_errors:
+        ws.check()
+    return Y, lam
+
+
 class GiniStress(torch.autograd.Function):
     """S(Y) = sum_{i<j} (Dbar(y_i, y_j) - delta_ij)^2 / sum_delta2 as an autograd op.
 
