@@ -298,6 +298,32 @@ int gini_fit_batched(const gini_problem* probs, int nprob, const double* nu_host
                      double* history_dev, double* final_stress_dev, int* tuned_config, void* ws,
                      size_t ws_bytes, void* stream);
 
+/* Bytes of workspace gini_nu_search needs (0 on invalid folds or sizes). */
+size_t gini_nu_search_workspace_size(int64_t n, int64_t p, const int32_t* fold_host, int K,
+                                     int n_nu, int restarts, int iters);
+
+/* The nu search of Algorithm 1: for every nu of the grid and every fold, the
+ * fold's dissimilarities (pairs of points of that fold only), `restarts` k = 2
+ * fits of `iters` steps as in gini_fit_batched, and KS = sqrt(S(Y_T)) of the
+ * best restart; nu* minimises the mean KS over the folds.  The folds are the
+ * problems of one gini_fit_batched call per 8 grid values.
+ *   X_dev        n x p floats, row stride ldx
+ *   fold_host    n fold labels in [0, K) (host); every fold needs >= 2 points
+ *   K            1..64 folds; n_nu 1..64 grid values, each > 1
+ *   Y0_dev       restarts x n x 2 floats: starting points in point order (a
+ *                point's start is the same for every nu)
+ *   ks_dev       n_nu x K doubles out (nu-major)
+ *   mean_ks_dev  n_nu doubles out
+ *   best_dev     one int out: the index of nu* in nu_host (the first minimiser)
+ *   Y_dev        n x 2 floats out: each point's embedding in its fold's best
+ *                restart at nu*
+ * Asynchronous on `stream` except where gini_fit_batched synchronises (its
+ * first call for a batch shape times the kernel candidates). */
+int gini_nu_search(const float* X_dev, int64_t n, int64_t p, int64_t ldx, const int32_t* fold_host,
+                   int K, const double* nu_host, int n_nu, int restarts, int iters, double eta0,
+                   const float* Y0_dev, double* ks_dev, double* mean_ks_dev, int* best_dev,
+                   float* Y_dev, void* ws, size_t ws_bytes, void* stream);
+
 /* Bytes of workspace gini_classical_mds needs. */
 size_t gini_cmds_workspace_size(int64_t n, int k);
 

@@ -2,9 +2,11 @@
 
 TEST INFRASTRUCTURE ONLY: tests/, __graft_entry__.smoke() and the CPU-baseline
 / reference arm of bench.py are the only users.  The product path never imports
-this module.  Every function but classical_mds forwards to the C oracle, whose
-header lists the paper passages each routine follows; classical_mds is the
-textbook definition in numpy (its eigensolver a library step).
+this module.  The per-pair and per-iteration functions forward to the C oracle,
+whose header lists the paper passages each routine follows; classical_mds is
+the textbook definition in numpy (its eigensolver a library step); nu_search
+composes delta and fit in the loops of Algorithm 1; default_step is the step
+rule's formula.
 """
 from __future__ import annotations
 
@@ -224,3 +226,43 @@ def classical_mds(Delta, k: int):
     idx = np.argsort(w)[::-1][:k]
     lam = w[idx]
     return V[:, idx] * np.sqrt(np.maximum(lam, 0.0)), lam
+
+
+def default_step(n, k, nu, sum_delta2, eta0=1.0):
+    """The fixed step the fits use (the paper gives none): eta0 over a
+    Gershgorin bound on the Gauss-Newton curvature of S,
+    eta0 * sum_delta2 / (2 (n-1) k ((k/2) w_max)^2), w_max = ((k-1)/k)^(nu-1)."""
+    if n < 2:
+        return 0.0
+    w = ((k - 1) / k) ** (nu - 1.0)
+    return eta0 * sum_delta2 / (2.0 * (n - 1) * k * (0.5 * k * w) ** 2)
+
+
+def nu_search(X, folds, nus, Y0, iters, eta0=1.0):
+    """Algorithm 1 as written: for each nu, for each fold, the fold's Delta,
+    `iters` fixed-step GD iterations from each start (Y0: restarts x n x 2, in
+    point order), KS = sqrt(S(Y_T)) of the best start; nu* = argmin of the mean
+    KS over folds (the first minimiser).  Returns (ks (n_nu, K), mean_ks, best,
+    Y (n, 2) of nu*'s fits)."""
+    X = np.asarray(X, dtype=np.float32)
+    folds = np.asarray(folds)
+    Y0 = np.asarray(Y0, dtype=np.float64)
+    K = int(folds.max()) + 1
+    n = X.shape[0]
+    ks = np.empty((len(nus), K))
+    Ys = np.empty((len(nus), n, 2))
+    for q in range(K):
+        idx = np.flatnonzero(folds == q)  # increasing point order
+        D, sd2 = delta(X[idx], nus)
+        for v, nu in enumerate(nus):
+            eta = default_step(len(idx), 2, nu, sd2[v], eta0)
+            best = np.inf
+            for r in range(Y0.shape[0]):
+                Yr, h = fit(D[v], nu, sd2[v], Y0[r][idx], eta, iters)
+                if h[-1] < best:
+                    best = h[-1]
+                    Ys[v][idx] = Yr
+            ks[v, q] = np.sqrt(best)
+    mean_ks = ks.mean(axis=1)
+    b = int(np.argmin(mean_ks))
+    return ks, mean_ks, b, Ys[b]

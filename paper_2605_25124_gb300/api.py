@@ -261,6 +261,42 @@ def gini_fit_batched(Xs, nus, restarts: int, iters: int, Y0: torch.Tensor, eta0:
             "tuned": tuned.value}
 
 
+def gini_nu_search(X: torch.Tensor, folds, nus, restarts: int, iters: int, Y0: torch.Tensor,
+                   eta0: float = 1.0, ws: Optional[Workspace] = None, check_errors: bool = True):
+    """Algorithm 1's search over a nu grid with K folds.  folds: n ints in [0, K)
+    (host sequence or array); Y0: (restarts, n, 2) float32 CUDA tensor.  Returns a
+    dict with "ks" ((n_nu, K) float64), "mean_ks" ((n_nu,)), "best" (index of
+    nu*, a 0-d int32 tensor) and "Y" ((n, 2): the fold embeddings at nu*)."""
+    _require_cuda(X)
+    assert X.dtype == torch.float32 and X.dim() == 2 and X.stride(1) == 1
+    n, p = X.shape
+    fold = np.ascontiguousarray(np.asarray(folds, dtype=np.int32))
+    assert fold.shape == (n,)
+    K = int(fold.max()) + 1 if n else 0
+    nus = [float(v) for v in nus]
+    n_nu = len(nus)
+    assert Y0.shape == (restarts, n, 2) and Y0.dtype == torch.float32
+    dev = X.device
+    fptr = fold.ctypes.data_as(ctypes.c_void_p)
+    nbytes = int(lib().gini_nu_search_workspace_size(n, p, fptr, K, n_nu, restarts, iters))
+    if nbytes == 0:
+        raise _lib.GiniError(_lib.GINI_EINVAL, "gini_nu_search_workspace_size")
+    ws = ws or workspace(dev)
+    buf = ws.ensure(nbytes)
+    ks = torch.empty((n_nu, K), dtype=torch.float64, device=dev)
+    mean_ks = torch.empty(n_nu, dtype=torch.float64, device=dev)
+    best = torch.empty((), dtype=torch.int32, device=dev)
+    Y = torch.empty((n, 2), dtype=torch.float32, device=dev)
+    nu_arr = (ctypes.c_double * n_nu)(*nus)
+    st = lib().gini_nu_search(_ptr(X), n, p, X.stride(0), fptr, K, nu_arr, n_nu, restarts, iters,
+                              float(eta0), _ptr(Y0.contiguous()), _ptr(ks), _ptr(mean_ks),
+                              _ptr(best), _ptr(Y), _ptr(buf), buf.numel(), _stream())
+    check(st, "gini_nu_search")
+    if check_errors:
+        ws.check()
+    return {"ks": ks, "mean_ks": mean_ks, "best": best, "Y": Y}
+
+
 def gini_classical_mds(D: Dissimilarity, k: int, iters: int = 20, seed: int = 0,
                        ws: Optional[Workspace] = None, check_errors: bool = True):
     """Classical MDS of D: (Y (n, k) float32, eigenvalues (k,) float64, descending)."""

@@ -1,0 +1,80 @@
+"""Algorithm 1's nu search over folds (gini_nu_search) against the oracle's
+composition of the same loops."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import gini_oracle as orc
+from paper_2605_25124_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+def _case(n, p, K, R, seed):
+    X = wl.gaussian_outliers(n, p, seed=seed)
+    folds = np.random.default_rng(seed).integers(0, K, size=n)
+    Y0 = wl.y_init(R * n, 2, seed=seed + 1, sd=1.0).reshape(R, n, 2)
+    return X, folds, Y0
+
+
+def test_search_matches_oracle(G):
+    # 10 grid values: two batched chunks (8 + 2); uneven random folds
+    n, p, K, R, T = 240, 6, 3, 2, 15
+    nus = list(np.linspace(1.2, 3.5, 10))
+    X, folds, Y0 = _case(n, p, K, R, 970)
+    out = G.gini_nu_search(torch.from_numpy(X).cuda(), folds, nus, R, T,
+                           torch.from_numpy(Y0).cuda())
+    ks, mean_ks, best, Y = orc.nu_search(X, folds, nus, Y0, T)
+    got = out["ks"].cpu().numpy()
+    assert np.max(np.abs(got - ks) / ks) <= 2e-4
+    assert np.max(np.abs(out["mean_ks"].cpu().numpy() - mean_ks) / mean_ks) <= 2e-4
+    srt = np.sort(mean_ks)
+    if srt[1] - srt[0] > 1e-3 * srt[0]:  # nu* unique beyond the tolerance
+        assert int(out["best"]) == best
+        Yg = out["Y"].cpu().numpy()
+        assert np.max(np.abs(Yg - Y)) <= 1e-3 * np.abs(Y).max()
+
+
+def test_search_planted_two_features(G):
+    # p = 2: each fold's Delta is the k = 2 embedding distance of its own rows,
+    # so starting from X every KS is ~0 (FP32 rounding) and Y returns X
+    n = 300
+    X = wl.gaussian_outliers(n, 2, seed=971)
+    folds = np.arange(n) % 4
+    Y0 = np.stack([X, X]).astype(np.float32)
+    out = G.gini_nu_search(torch.from_numpy(X).cuda(), folds, [1.3, 2.0, 4.0], 2, 5,
+                           torch.from_numpy(Y0).cuda())
+    assert np.all(out["ks"].cpu().numpy() < 1e-5)
+    Yg = out["Y"].cpu().numpy()
+    assert np.max(np.abs(Yg - X)) <= 1e-5 * np.abs(X).max()
+
+
+def test_one_fold_is_the_batched_fit(G):
+    n, p, R, T = 200, 5, 3, 10
+    nus = [1.5, 2.0, 3.0]
+    X, _, Y0 = _case(n, p, 1, R, 972)
+    Xd = torch.from_numpy(X).cuda()
+    out = G.gini_nu_search(Xd, np.zeros(n, dtype=np.int32), nus, R, T,
+                           torch.from_numpy(Y0).cuda())
+    ref = G.gini_fit_batched([Xd], nus, R, T, torch.from_numpy(Y0.reshape(-1).copy()).cuda())
+    want = np.sqrt(ref["final"].cpu().numpy()[0].min(axis=1))
+    # the same fits, up to the order of the kernel's FP32 column-sum atomics
+    np.testing.assert_allclose(out["ks"].cpu().numpy()[:, 0], want, rtol=1e-6)
+    assert int(out["best"]) == int(np.argmin(want))
+
+
+def test_search_argument_errors(G):
+    from paper_2605_25124_gb300._lib import GiniError
+    n = 50
+    X, _, Y0 = _case(n, 4, 1, 1, 973)
+    Xd, Y0d = torch.from_numpy(X).cuda(), torch.from_numpy(Y0).cuda()
+    lonely = np.zeros(n, dtype=np.int32)
+    lonely[7] = 1  # a fold with one point has no pair
+    with pytest.raises(GiniError, match="EINVAL"):
+        G.gini_nu_search(Xd, lonely, [2.0], 1, 5, Y0d)
+    with pytest.raises(GiniError, match="EINVAL"):
+        G.gini_nu_search(Xd, np.zeros(n, dtype=np.int32), [1.0], 1, 5, Y0d)
+    X2, _, Y02 = _case(200, 4, 1, 1, 974)
+    with pytest.raises(GiniError, match="EINVAL"):  # 65 folds
+        G.gini_nu_search(torch.from_numpy(X2).cuda(), np.arange(200) % 65, [2.0], 1, 5,
+                         torch.from_numpy(Y02).cuda())
