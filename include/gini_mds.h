@@ -324,6 +324,33 @@ int gini_nu_search(const float* X_dev, int64_t n, int64_t p, int64_t ldx, const 
                    const float* Y0_dev, double* ks_dev, double* mean_ks_dev, int* best_dev,
                    float* Y_dev, void* ws, size_t ws_bytes, void* stream);
 
+/* Bytes of workspace gini_alternating_nu needs. */
+size_t gini_alternating_nu_workspace_size(int64_t n, int64_t p, int k, int n_nu, int iters);
+
+/* The alternating nu update of the heavy-tail experiment (Algorithm 2): from
+ * nu_0 = nu_start, for t = 0 .. rounds-1: fit Y (gini_mds_fit, `iters` steps
+ * of the given metric and loss, warm-started from the previous round) on
+ * Delta_{nu_t}; then KS(nu) = sqrt(Kruskal stress) of that fixed Y against
+ * Delta_nu for every nu of the grid (the same metric), and nu_{t+1} = the first
+ * minimiser.  Delta is built once for the grid and nu_start (tiled F32, kept in
+ * the workspace).  The step is eta0 over a Gershgorin bound on the
+ * Gauss-Newton curvature of the loss: with c = k ((k/2) w_max)^2 (Gini
+ * metric) or 1 (Euclidean),
+ *   Kruskal: eta = eta0 sum delta^2 / (2 (n-1) c)
+ *   Sammon:  eta = eta0 sum delta / (2 c max_i sum_{j: delta_ij > 0} 1/delta_ij).
+ *   X_dev         n x p floats (p <= 1024), row stride ldx
+ *   nu_host       n_nu (1..64) grid values, each > 1; nu_start > 1
+ *   k             2..8; metric gini_metric; loss gini_loss (Algorithm 2: Sammon)
+ *   Y_dev         n x k floats, in: Y_0, out: the last round's fit
+ *   nu_path_host  rounds + 1 doubles out: nu_0 .. nu_rounds
+ *   ks_host       rounds x n_nu doubles out: KS(nu) after each round's fit
+ * Synchronises `stream` (the host chooses each round's nu); device-side errors
+ * are returned directly.  GINI_EDEGENERATE if some Delta is all zero. */
+int gini_alternating_nu(const float* X_dev, int64_t n, int64_t p, int64_t ldx, int k,
+                        const double* nu_host, int n_nu, double nu_start, int rounds, int iters,
+                        double eta0, int metric, int loss, float* Y_dev, double* nu_path_host,
+                        double* ks_host, void* ws, size_t ws_bytes, void* stream);
+
 /* Bytes of workspace gini_classical_mds needs. */
 size_t gini_cmds_workspace_size(int64_t n, int k);
 

@@ -5,8 +5,8 @@ TEST INFRASTRUCTURE ONLY: tests/, __graft_entry__.smoke() and the CPU-baseline
 this module.  The per-pair and per-iteration functions forward to the C oracle,
 whose header lists the paper passages each routine follows; classical_mds is
 the textbook definition in numpy (its eigensolver a library step); nu_search
-composes delta and fit in the loops of Algorithm 1; default_step is the step
-rule's formula.
+composes delta and fit in the loops of Algorithm 1 and alternating_nu those of
+Algorithm 2; default_step is the step rule's formula.
 """
 from __future__ import annotations
 
@@ -266,3 +266,50 @@ def nu_search(X, folds, nus, Y0, iters, eta0=1.0):
     mean_ks = ks.mean(axis=1)
     b = int(np.argmin(mean_ks))
     return ks, mean_ks, b, Ys[b]
+
+
+def _curv(metric, k, nu):
+    if metric == "euclid":
+        return 1.0
+    w = ((k - 1) / k) ** (nu - 1.0)
+    return k * (0.5 * k * w) ** 2
+
+
+def alternating_nu(X, nus, nu_start, rounds, iters, Y0, eta0=1.0, metric="gini",
+                   loss="sammon"):
+    """Algorithm 2's alternation as written: fit at the current nu (fixed-step
+    GD on the loss, warm-started), then nu <- the first grid value minimising
+    the Kruskal stress KS(nu) of the fixed embedding.  The step is eta0 over a
+    Gershgorin bound on the Gauss-Newton curvature (Kruskal:
+    sum delta^2 / (2 (n-1) c), Sammon: sum delta / (2 c max_i sum_j 1/delta_ij)).
+    Returns (Y, nu path, KS table (rounds, n_nu))."""
+    allnus = list(nus) + [nu_start]
+    D, s2 = delta(X, allnus)
+    n = D.shape[1]
+    iu = np.triu_indices(n, 1)
+    s1 = np.array([D[v][iu].sum() for v in range(len(allnus))])
+    Y = np.array(Y0, dtype=np.float64)
+    k = Y.shape[1]
+    cur = len(nus)
+    path, table = [nu_start], []
+    for _ in range(rounds):
+        nu = allnus[cur]
+        c = _curv(metric, k, nu)
+        if loss == "kruskal":
+            norm = s2[cur]
+            eta = eta0 * norm / (2.0 * (n - 1) * c)
+        else:
+            norm = s1[cur]
+            Dc = D[cur].copy()
+            np.fill_diagonal(Dc, 0.0)
+            inv = np.where(Dc > 0, 1.0 / np.where(Dc > 0, Dc, 1.0), 0.0)
+            eta = eta0 * norm / (2.0 * c * inv.sum(axis=1).max())
+        for _ in range(iters):
+            _, g = stress_grad_ex(Y, nu, D[cur], norm, metric, loss)
+            Y = Y - eta * g
+        row = [np.sqrt(stress_grad_ex(Y, nus[v], D[v], s2[v], metric, "kruskal",
+                                      grad=False)[0]) for v in range(len(nus))]
+        table.append(row)
+        cur = int(np.argmin(row))
+        path.append(nus[cur])
+    return Y, path, np.array(table)

@@ -297,6 +297,34 @@ def gini_nu_search(X: torch.Tensor, folds, nus, restarts: int, iters: int, Y0: t
     return {"ks": ks, "mean_ks": mean_ks, "best": best, "Y": Y}
 
 
+def gini_alternating_nu(X: torch.Tensor, nus, nu_start: float, rounds: int, iters: int,
+                        Y0: torch.Tensor, eta0: float = 1.0, metric: str = "gini",
+                        loss: str = "sammon", ws: Optional[Workspace] = None):
+    """Algorithm 2's alternating nu update.  Returns (Y (n, k) float32 CUDA tensor,
+    nu path (rounds + 1 floats), KS table ((rounds, n_nu) float64 numpy array))."""
+    _require_cuda(X)
+    assert X.dtype == torch.float32 and X.dim() == 2 and X.stride(1) == 1
+    n, p = X.shape
+    k = Y0.shape[1]
+    assert Y0.shape == (n, k) and Y0.dtype == torch.float32
+    nus = [float(v) for v in nus]
+    n_nu = len(nus)
+    Y = Y0.clone().contiguous()
+    nbytes = int(lib().gini_alternating_nu_workspace_size(n, p, k, n_nu, iters))
+    ws = ws or workspace(X.device)
+    buf = ws.ensure(nbytes)
+    nu_arr = (ctypes.c_double * n_nu)(*nus)
+    path = (ctypes.c_double * (rounds + 1))()
+    ks = np.zeros((rounds, n_nu), dtype=np.float64)
+    st = lib().gini_alternating_nu(_ptr(X), n, p, X.stride(0), k, nu_arr, n_nu, float(nu_start),
+                                   int(rounds), int(iters), float(eta0), METRICS[metric],
+                                   LOSSES[loss], _ptr(Y), path,
+                                   ks.ctypes.data_as(ctypes.c_void_p), _ptr(buf), buf.numel(),
+                                   _stream())
+    check(st, "gini_alternating_nu")
+    return Y, list(path), ks
+
+
 def gini_classical_mds(D: Dissimilarity, k: int, iters: int = 20, seed: int = 0,
                        ws: Optional[Workspace] = None, check_errors: bool = True):
     """Classical MDS of D: (Y (n, k) float32, eigenvalues (k,) float64, descending)."""
