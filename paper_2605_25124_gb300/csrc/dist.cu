@@ -11,9 +11,10 @@
 // its positional weights and the run bookkeeping is skipped (exactly equal).
 //
 // Work split: CTA = 8 warps = 8 consecutive rows i; blockIdx.x picks a block
-// of CB columns j.  A warp keeps x_i in registers and walks its columns, each
-// of the 32/L segments taking every (32/L)-th j.  X is read through L2 (a row
-// is a few KB; the per-pair compute dwarfs the traffic).
+// of CB columns j.  A warp keeps x_i in shared memory (in registers it would
+// cost the 32 registers that let two CTAs share an SM) and walks its columns,
+// each of the 32/L segments taking every (32/L)-th j.  X is read through L2 (a
+// row is a few KB; the per-pair compute dwarfs the traffic).
 #include <math.h>
 #include <stdio.h>
 
@@ -98,12 +99,13 @@ k_dist(const DistParams P) {
 
   const int64_t i = row0 + warp;
   const bool row_ok = i < P.n - 1;
-  float xi[E];
+  __shared__ float s_xi[DIST_WARPS][E * L];
 #pragma unroll
   for (int t = 0; t < E; ++t) {
     const int e = t * L + ls;
-    xi[t] = (row_ok && e < m) ? __ldg(P.X + i * P.ldx + e) : 0.f;
+    if (seg == 0) s_xi[warp][e] = (row_ok && e < m) ? __ldg(P.X + i * P.ldx + e) : 0.f;
   }
+  __syncwarp();
 
   double sd2[NQ];
 #pragma unroll
@@ -119,7 +121,7 @@ k_dist(const DistParams P) {
     for (int t = 0; t < E; ++t) {
       const int e = t * L + ls;
       float xj = (active && e < m) ? __ldg(P.X + j * P.ldx + e) : 0.f;
-      v[t] = (e < m) ? xi[t] - xj : __int_as_float(0x7f800000);  // pad with +inf
+      v[t] = (e < m) ? s_xi[warp][e] - xj : __int_as_float(0x7f800000);  // pad with +inf
     }
     seg_bitonic_sort<E, L>(v, ls);
 
@@ -210,7 +212,8 @@ static cudaError_t launch_dist(const DistParams& P, cudaStream_t s) {
   const int tab_n = 2 * m - 1;
   const int tab_stride = tab_n - 1 + (tab_n - 1) / (2 * E) + 1;
   const size_t smem = AFFINE ? 0 : (size_t)P.n_nu * tab_stride * sizeof(float);
-  if (smem > 48 * 1024) {
+  // static (x_i rows) + dynamic (weight tables) may pass the 48 KB default
+  if (smem > 0) {
     cudaError_t e = cudaFuncSetAttribute(k_dist<E, L, AFFINE>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

@@ -936,7 +936,7 @@ static void full_k(int k, const IterParams& Q, cudaStream_t s) {
 template <int K, int DT, bool GRAD>
 static void launch_fusedk(unsigned g, const IterParams& Q, int64_t ntiles, cudaStream_t s) {
   const size_t smem = sizeof(FusedKSmem<K>);
-  if (smem > 48 * 1024)
+  if (smem + 1024 > 48 * 1024)  // plus the kernel's static shared memory
     cudaFuncSetAttribute(k_fusedk<K, DT, GRAD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
   gini_count_launch(1);

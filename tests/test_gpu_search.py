@@ -60,7 +60,9 @@ def test_one_fold_is_the_batched_fit(G):
     want = np.sqrt(ref["final"].cpu().numpy()[0].min(axis=1))
     # the same fits, up to the order of the kernel's FP32 column-sum atomics
     np.testing.assert_allclose(out["ks"].cpu().numpy()[:, 0], want, rtol=1e-6)
-    assert int(out["best"]) == int(np.argmin(want))
+    # nu = 2 and nu = 3 tie exactly (W_3 is proportional to W_2), so check the
+    # chosen value is a minimiser rather than which of the tied ones it is
+    assert want[int(out["best"])] <= want.min() * (1 + 1e-6)
 
 
 def test_search_argument_errors(G):
