@@ -184,9 +184,12 @@ __global__ void __launch_bounds__(256) k_full(const IterParams Q) {
     for (int c = 0; c < K; ++c) acc[c] = 0.f;
     float S = 0.f, Sc = 0.f;  // compensated FP32 sum over the row
     const bool fast2 = scalar2_path(K, Q.metric, Q.loss);
-    for (int64_t j = (FWD ? i + 1 : 0) + lane; j < Q.n; j += 32) {
-      const float dl = __ldcs(D + i * Q.ldd + j);
-      if (K == 2 && fast2) {
+    if (K == 2 && fast2) {
+      // Gini metric, Kruskal loss, k = 2: its own loop, so the streaming loads
+      // of several columns can be in flight at once
+#pragma unroll 4
+      for (int64_t j = (FWD ? i + 1 : 0) + lane; j < Q.n; j += 32) {
+        const float dl = __ldcs(D + i * Q.ldd + j);
         float r, t;
         pair2(Pi[0], Q.P[j], Q.tab.c2, dl, r, t);
         if (FWD) {
@@ -197,7 +200,10 @@ __global__ void __launch_bounds__(256) k_full(const IterParams Q) {
         } else if (j != i) {
           acc[0] += t;
         }
-      } else {
+      }
+    } else {
+      for (int64_t j = (FWD ? i + 1 : 0) + lane; j < Q.n; j += 32) {
+        const float dl = __ldcs(D + i * Q.ldd + j);
         float yj[K], dw[K];
 #pragma unroll
         for (int c = 0; c < K; ++c) yj[c] = Q.Y[j * K + c];
