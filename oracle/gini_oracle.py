@@ -6,7 +6,9 @@ this module.  The per-pair and per-iteration functions forward to the C oracle,
 whose header lists the paper passages each routine follows; classical_mds is
 the textbook definition in numpy (its eigensolver a library step); nu_search
 composes delta and fit in the loops of Algorithm 1 and alternating_nu those of
-Algorithm 2; default_step is the step rule's formula.
+Algorithm 2; default_step is the step rule's formula; the evaluation measures
+of Section V (trustworthiness, NN(k), silhouette, distance correlations) are
+their definitions in numpy.
 """
 from __future__ import annotations
 
@@ -313,3 +315,95 @@ def alternating_nu(X, nus, nu_start, rounds, iters, Y0, eta0=1.0, metric="gini",
         cur = int(np.argmin(row))
         path.append(nus[cur])
     return Y, path, np.array(table)
+
+
+# --- Evaluation measures of Section V (plain definitions, FP64) -------------
+
+def sq_dists(A):
+    """Squared Euclidean distances of the rows of A, in float64."""
+    A = np.asarray(A, dtype=np.float64)
+    return ((A[:, None, :] - A[None, :, :]) ** 2).sum(-1)
+
+
+def _order(d_row, i):
+    """Indices of the other points by increasing (distance, index)."""
+    n = d_row.shape[0]
+    idx = np.array([l for l in range(n) if l != i])
+    return idx[np.lexsort((idx, d_row[idx]))]
+
+
+def trustworthiness(X, Y, k):
+    """T(k) = 1 - 2/(n k (2n - 3k - 1)) sum_i sum_{j in N_i} max(0, r(i, j) - k):
+    N_i the k nearest neighbours of i in the embedding, r(i, j) the rank of j
+    among the original-space distances from i (1 = nearest); Euclidean in both
+    spaces, ties broken by the smaller index."""
+    dX, dY = sq_dists(X), sq_dists(Y)
+    n = dX.shape[0]
+    total = 0
+    for i in range(n):
+        rank = np.empty(n, dtype=np.int64)
+        rank[_order(dX[i], i)] = np.arange(1, n)
+        for j in _order(dY[i], i)[:k]:
+            total += max(0, rank[j] - k)
+    return 1.0 - 2.0 * total / (n * k * (2.0 * n - 3.0 * k - 1.0))
+
+
+def nn_agreement(Y, labels, k):
+    """NN(k) = (1/(n k)) sum_i sum_{j in N_i} [label_j = label_i], N_i the k
+    nearest neighbours of i in the embedding (Euclidean, ties by index)."""
+    dY = sq_dists(Y)
+    labels = np.asarray(labels)
+    n = dY.shape[0]
+    hits = sum(int(np.sum(labels[_order(dY[i], i)[:k]] == labels[i])) for i in range(n))
+    return hits / (n * k)
+
+
+def silhouette(Y, labels):
+    """Mean of s_i = (b_i - a_i) / max(a_i, b_i): a_i the mean distance to the
+    other points of i's label, b_i the smallest mean distance to another
+    label's points; s_i = 0 when i's label has no other point."""
+    D = np.sqrt(sq_dists(Y))
+    labels = np.asarray(labels)
+    n = D.shape[0]
+    s = np.zeros(n)
+    classes = np.unique(labels)
+    for i in range(n):
+        own = labels == labels[i]
+        if own.sum() <= 1:
+            continue
+        a = D[i][own].sum() / (own.sum() - 1)
+        b = min(D[i][labels == c].mean() for c in classes if c != labels[i])
+        s[i] = (b - a) / max(a, b)
+    return float(s.mean())
+
+
+def _pearson(u, v):
+    u = np.asarray(u, dtype=np.float64)
+    v = np.asarray(v, dtype=np.float64)
+    du, dv = u - u.mean(), v - v.mean()
+    return float((du * dv).sum() / np.sqrt((du * du).sum() * (dv * dv).sum()))
+
+
+def midranks(v):
+    """1-based ranks of v with ties given the mean of their positions."""
+    v = np.asarray(v)
+    order = np.argsort(v, kind="stable")
+    r = np.empty(len(v))
+    sv = v[order]
+    s = 0
+    while s < len(v):
+        e = s
+        while e + 1 < len(v) and sv[e + 1] == sv[s]:
+            e += 1
+        r[order[s:e + 1]] = (s + e) / 2.0 + 1.0
+        s = e + 1
+    return r
+
+
+def distance_correlations(X, Y):
+    """(Pearson, Spearman) correlation between the n(n-1)/2 pairwise Euclidean
+    distances of X and those of Y (pairs i < j; Spearman = Pearson of midranks)."""
+    iu = np.triu_indices(np.asarray(X).shape[0], 1)
+    dx = np.sqrt(sq_dists(X)[iu])
+    dy = np.sqrt(sq_dists(Y)[iu])
+    return _pearson(dx, dy), _pearson(midranks(dx), midranks(dy))
