@@ -376,6 +376,48 @@ int gini_classical_mds(const void* delta_dev, int64_t n, int layout, int dtype, 
                        float* Y_dev, double* eigvals_dev, void* ws, size_t ws_bytes,
                        void* stream);
 
+/* Evaluation measures of an embedding (Section V-A and the heavy-tail
+ * experiment).  Distances are Euclidean in both spaces; every decision that
+ * turns distances into integers (the k nearest neighbours, ranks) compares
+ * FP64 squared distances of the FP32 inputs (products and sums rounded
+ * separately, features summed in order), ties going to the smaller index.
+ * Results are written to device memory; nothing synchronises. */
+
+/* Bytes of workspace the evaluation calls need: n points, n_labels labels
+ * (silhouette), spearman != 0 for gini_distance_correlations with ranks (about
+ * 40 bytes per pair of points; without, a few hundred bytes). */
+size_t gini_eval_workspace_size(int64_t n, int n_labels, int spearman);
+
+/* out_dev[0] = trustworthiness T(k_trust) = 1 - 2 / (n k (2n - 3k - 1)) *
+ *   sum_i sum_{j in N_i} max(0, r(i, j) - k), N_i the k nearest neighbours of i
+ *   in the embedding, r(i, j) the rank of j by distance from i in the data
+ *   (1 = nearest); NaN when k_trust = 0.
+ * out_dev[1] = NN(k_nn) = (1 / (n k)) sum_i #{j in N_i: label_j = label_i}
+ *   (N_i the k_nn nearest embedding neighbours); NaN when k_nn = 0.
+ *   X_dev n x p (row stride ldx), Y_dev n x k (k <= 8), labels_dev n int32 or
+ *   NULL when k_nn = 0; 0 <= k_trust, k_nn <= 64, both < n.  One CTA per point;
+ *   the data-space pass costs n^2 p FP64 multiply-adds. */
+int gini_neighbour_scores(const float* X_dev, int64_t n, int64_t p, int64_t ldx,
+                          const float* Y_dev, int k, const int32_t* labels_dev, int k_trust,
+                          int k_nn, double* out_dev, void* ws, size_t ws_bytes, void* stream);
+
+/* out_dev[0] = silhouette score (1/n) sum_i (b_i - a_i) / max(a_i, b_i) of the
+ * embedding: a_i the mean distance from i to the other points of its label,
+ * b_i the smallest mean distance to the points of another label; s_i = 0 when
+ * i's label has no other point or no other label has points.  labels_dev: n
+ * int32 in [0, n_labels), n_labels 1..64 (a label outside is reported as
+ * GINI_ENONFINITE by gini_check and ignored). */
+int gini_silhouette(const float* Y_dev, int64_t n, int k, const int32_t* labels_dev, int n_labels,
+                    double* out_dev, void* ws, size_t ws_bytes, void* stream);
+
+/* out_dev[0] = Pearson and out_dev[1] = Spearman correlation between the
+ * n(n-1)/2 pairwise Euclidean distances of X and those of Y (pairs i < j;
+ * Spearman = Pearson of midranks, from a device radix sort of the FP64
+ * distances; NaN when spearman = 0).  2 <= n <= 65535. */
+int gini_distance_correlations(const float* X_dev, int64_t n, int64_t p, int64_t ldx,
+                               const float* Y_dev, int k, int spearman, double* out_dev, void* ws,
+                               size_t ws_bytes, void* stream);
+
 /* A step size for gini_mds_fit: eta0 times the inverse of a Gershgorin bound
  * on the Gauss-Newton curvature of S,
  *   eta = eta0 * sum_delta2 / (2 (n-1) k ((k/2) w_max)^2),  w_max = ((k-1)/k)^{nu-1}.

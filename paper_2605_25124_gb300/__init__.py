@@ -5,9 +5,9 @@ include/gini_mds.h); this package is its thin Python binding.  `workloads`
 holds the seeded synthetic input generators.
 """
 from .api import (Dissimilarity, GiniStress, Workspace, default_step, fit_host, gini_dist,
-                  gini_alternating_nu, gini_classical_mds, gini_delta_sums, gini_fit_batched, gini_mds_fit, gini_nu_search, gini_pack, gini_rank, gini_stress, gini_stress_grad, tile_size,
+                  gini_alternating_nu, gini_classical_mds, gini_delta_sums, gini_distance_correlations, gini_fit_batched, gini_mds_fit, gini_neighbour_scores, gini_nu_search, gini_silhouette, gini_pack, gini_rank, gini_stress, gini_stress_grad, tile_size,
                   tiled_elems, workspace, workspace_size)
 
 __all__ = ["Dissimilarity", "GiniStress", "Workspace", "default_step", "fit_host", "gini_dist",
-           "gini_alternating_nu", "gini_classical_mds", "gini_delta_sums", "gini_fit_batched", "gini_mds_fit", "gini_nu_search", "gini_pack", "gini_rank", "gini_stress", "gini_stress_grad",
+           "gini_alternating_nu", "gini_classical_mds", "gini_delta_sums", "gini_distance_correlations", "gini_fit_batched", "gini_mds_fit", "gini_neighbour_scores", "gini_nu_search", "gini_silhouette", "gini_pack", "gini_rank", "gini_stress", "gini_stress_grad",
            "tile_size", "tiled_elems", "workspace", "workspace_size"]

@@ -325,6 +325,64 @@ def gini_alternating_nu(X: torch.Tensor, nus, nu_start: float, rounds: int, iter
     return Y, list(path), ks
 
 
+def _xy(X, Y):
+    _require_cuda(X)
+    assert X.dtype == torch.float32 and X.dim() == 2 and X.stride(1) == 1
+    assert Y.dtype == torch.float32 and Y.is_contiguous() and Y.shape[0] == X.shape[0]
+    return X.shape[0], X.shape[1], Y.shape[1]
+
+
+def gini_neighbour_scores(X: torch.Tensor, Y: torch.Tensor, labels: Optional[torch.Tensor] = None,
+                          k_trust: int = 5, k_nn: int = 10, ws: Optional[Workspace] = None):
+    """(T(k_trust), NN(k_nn)) as a float64 CUDA tensor of 2 (NaN where not asked)."""
+    n, p, k = _xy(X, Y)
+    if labels is None:
+        k_nn = 0
+    else:
+        assert labels.dtype == torch.int32 and labels.is_contiguous() and labels.numel() == n
+    out = torch.empty(2, dtype=torch.float64, device=X.device)
+    ws = ws or workspace(X.device)
+    buf = ws.ensure(int(lib().gini_eval_workspace_size(n, 1, 0)))
+    st = lib().gini_neighbour_scores(_ptr(X), n, p, X.stride(0), _ptr(Y), k, _ptr(labels),
+                                     int(k_trust), int(k_nn), _ptr(out), _ptr(buf), buf.numel(),
+                                     _stream())
+    check(st, "gini_neighbour_scores")
+    return out
+
+
+def gini_silhouette(Y: torch.Tensor, labels: torch.Tensor, n_labels: Optional[int] = None,
+                    ws: Optional[Workspace] = None, check_errors: bool = True):
+    """Silhouette score of the embedding under integer labels in [0, n_labels)."""
+    _require_cuda(Y)
+    assert Y.dtype == torch.float32 and Y.is_contiguous()
+    assert labels.dtype == torch.int32 and labels.is_contiguous()
+    n, k = Y.shape
+    if n_labels is None:
+        n_labels = int(labels.max().item()) + 1
+    out = torch.empty(1, dtype=torch.float64, device=Y.device)
+    ws = ws or workspace(Y.device)
+    buf = ws.ensure(int(lib().gini_eval_workspace_size(n, n_labels, 0)))
+    st = lib().gini_silhouette(_ptr(Y), n, k, _ptr(labels), int(n_labels), _ptr(out), _ptr(buf),
+                               buf.numel(), _stream())
+    check(st, "gini_silhouette")
+    if check_errors:
+        ws.check()
+    return out[0]
+
+
+def gini_distance_correlations(X: torch.Tensor, Y: torch.Tensor, spearman: bool = True,
+                               ws: Optional[Workspace] = None):
+    """(Pearson, Spearman) between pairwise distances of X and of Y (float64 tensor of 2)."""
+    n, p, k = _xy(X, Y)
+    out = torch.empty(2, dtype=torch.float64, device=X.device)
+    ws = ws or workspace(X.device)
+    buf = ws.ensure(int(lib().gini_eval_workspace_size(n, 1, int(spearman))))
+    st = lib().gini_distance_correlations(_ptr(X), n, p, X.stride(0), _ptr(Y), k, int(spearman),
+                                          _ptr(out), _ptr(buf), buf.numel(), _stream())
+    check(st, "gini_distance_correlations")
+    return out
+
+
 def gini_classical_mds(D: Dissimilarity, k: int, iters: int = 20, seed: int = 0,
                        ws: Optional[Workspace] = None, check_errors: bool = True):
     """Classical MDS of D: (Y (n, k) float32, eigenvalues (k,) float64, descending)."""
