@@ -143,39 +143,62 @@ __global__ void __launch_bounds__(TILE / ROWS * 32) k_batch_iter(const BatchPara
     }
     __syncthreads();
     const bool masked = (I == J) || (i0 + TILE > n) || (j0 + TILE > n);
+    const float2 k64 = make_float2(0x1p64f, 0x1p64f);
+    const float2 k126 = make_float2(0x1p126f, 0x1p126f);
+    const float2 m1 = make_float2(-1.f, -1.f);
+    const float2 nc2 = make_float2(-sg.c2, -sg.c2);
     for (int r = 0; r < R; ++r) {
       float rowv[ROWS];
-      float col[4] = {0.f, 0.f, 0.f, 0.f};
-      float S = 0.f;
-      float2 uc[4];
+      float2 col2[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+      float2 S2 = make_float2(0.f, 0.f);
+      // columns 4l+2p, 4l+2p+1 as packed pairs, negated: s = u_i - u_j = u_i + (-u_j)
+      float2 nuh[2], nul[2];
 #pragma unroll
-      for (int c = 0; c < 4; ++c) uc[c] = s_u[1][r][4 * lane + c];
+      for (int p = 0; p < 2; ++p) {
+        const float2 a = s_u[1][r][4 * lane + 2 * p], b = s_u[1][r][4 * lane + 2 * p + 1];
+        nuh[p] = make_float2(-a.x, -b.x);
+        nul[p] = make_float2(-a.y, -b.y);
+      }
 #pragma unroll
       for (int q = 0; q < ROWS; ++q) {
         const int rl = warp * ROWS + q;
         const float2 ur = s_u[0][r][rl];
-        const float dv[4] = {d[q].x, d[q].y, d[q].z, d[q].w};
-        float ra = 0.f;
+        const float2 uh2 = make_float2(ur.x, ur.x), ul2 = make_float2(ur.y, ur.y);
+        const float2 dv[2] = {make_float2(d[q].x, d[q].y), make_float2(d[q].z, d[q].w)};
+        float2 row2 = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          const float dh = ur.x - uc[c].x, dl = ur.y - uc[c].y;
-          const float sgv = (dh != 0.f) ? dh : dl;  // exact sign of u_i - u_j
-          float rv = fmaf(sg.c2, fabsf(dh + dl), -dv[c]);
+        for (int p = 0; p < 2; ++p) {
+          const float2 dh = __fadd2_rn(uh2, nuh[p]);
+          const float2 dlo = __fadd2_rn(ul2, nul[p]);
+          const float2 s2 = __fadd2_rn(dh, dlo);
+          // exact sign of u_i - u_j on the FMA pipe: dh dominates dlo unless it is
+          // zero; the scalings take any nonzero value, subnormals included, to
+          // >= 1 so the saturations give 1 / 0 per side
+          const float2 b2 = __fmul2_rn(__ffma2_rn(dh, k64, dlo), k126);
+          const float2 pp = make_float2(__saturatef(b2.x * 0x1p24f), __saturatef(b2.y * 0x1p24f));
+          const float2 qq = make_float2(__saturatef(-b2.x * 0x1p24f), __saturatef(-b2.y * 0x1p24f));
+          const float2 sig = __ffma2_rn(qq, m1, pp);
+          float2 rp = __ffma2_rn(nc2, __fmul2_rn(s2, sig), dv[p]);  // r' = delta - c2 |s|
           if (masked) {
-            const int cl = 4 * lane + c;
-            const bool ok = (i0 + rl < n) && (j0 + cl < n) && (I != J || rl < cl);
-            rv = ok ? rv : 0.f;
+            const int cl = 4 * lane + 2 * p;
+            const bool rok = i0 + rl < n;
+            const bool ok0 = rok && (j0 + cl < n) && (I != J || rl < cl);
+            const bool ok1 = rok && (j0 + cl + 1 < n) && (I != J || rl < cl + 1);
+            rp.x = ok0 ? rp.x : 0.f;
+            rp.y = ok1 ? rp.y : 0.f;
           }
-          S = fmaf(rv, rv, S);
+          S2 = __ffma2_rn(rp, rp, S2);
           if (GRAD) {
-            const float t = __int_as_float(__float_as_int(rv) ^ (__float_as_int(sgv) & 0x80000000));
-            const float tt = (sgv == 0.f) ? 0.f : t;
-            ra += tt;
-            col[c] -= tt;
+            const float2 tp = __fmul2_rn(rp, sig);  // -(r sign(s))
+            row2 = __fadd2_rn(row2, tp);
+            col2[p] = __fadd2_rn(col2[p], tp);
           }
         }
-        rowv[q] = ra;
+        rowv[q] = -(row2.x + row2.y);
       }
+      float S = S2.x + S2.y;
+      // column j receives -r sign(s), which is what the packed sums hold
+      const float col[4] = {col2[0].x, col2[0].y, col2[1].x, col2[1].y};
       // stress of this (fit, tile)
 #pragma unroll
       for (int o = 16; o >= 1; o >>= 1) S += __shfl_xor_sync(FULL_MASK, S, o);
