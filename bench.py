@@ -76,6 +76,12 @@ def _barrier(world):
         dist.barrier()
 
 
+def _replica_rate(units_per_rank, seconds, world):
+    """Whole-job throughput of `world` replicas: every rank processed
+    units_per_rank units; the job took as long as the slowest rank."""
+    return world * units_per_rank / _max_over_ranks(seconds, world)
+
+
 def _max_over_ranks(v, world):
     if world == 1:
         return v
@@ -229,8 +235,7 @@ def run_ours(args, rank, local, world):
     build_ms = [e[0].elapsed_time(e[1]) for e in evs]
     iter_ms = [e[1].elapsed_time(e[2]) for e in evs]
     step_ms = [a + b for a, b in zip(build_ms, iter_ms)]
-    total_s = _max_over_ranks(sum(step_ms) / 1e3, world)
-    value = world * T * args.steps / total_s
+    value = _replica_rate(T * args.steps, sum(step_ms) / 1e3, world)
     final_stress = float(finals[-1])
     clocks = clk.summary()
 
@@ -367,8 +372,7 @@ def _e2e(G, X_host, Y0_host, n, p, k, nu, T, args, world):
         t1 = time.perf_counter()
         if i >= args.warmup:
             ts.append(t1 - t0)
-    tot = _max_over_ranks(sum(ts), world)
-    return {"value": round(world * T * args.steps / tot, 3), "unit": "iters/s",
+    return {"value": round(_replica_rate(T * args.steps, sum(ts), world), 3), "unit": "iters/s",
             "h2d_bytes_per_step": int(X_host.nbytes + Y0_host.nbytes),
             "d2h_bytes_per_step": int(Y0_host.nbytes + 8)}
 
@@ -490,12 +494,12 @@ def run_batched(args, rank, local, world):
             torch.cuda.synchronize()
             times.append(e0.elapsed_time(e1))
     G.workspace(dev).check()
-    total_s = _max_over_ranks(sum(times) / 1e3, world)
+    rate = _replica_rate(nfits * T * args.steps, sum(times) / 1e3, world)
     pairs = sum(n * (n - 1) // 2 for n in ns) * len(nus)
     fin = out["final"].cpu().numpy()
     best_nu = [nus[int(np.argmin(fin[q].min(axis=1)))] for q in range(len(ns))]
     res = {"metric": "batched Gini-MDS fit iterations/s (all fits)", "value":
-           round(world * nfits * T * args.steps / total_s, 1), "unit": "fit-iters/s",
+           round(rate, 1), "unit": "fit-iters/s",
            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": round(statistics.mean(times), 3), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
