@@ -22,7 +22,8 @@
  *   - Pointers named *_dev are device memory owned by the caller; pointers
  *     named *_host are host memory owned by the caller.  The library never
  *     allocates device memory: scratch space comes from the caller's
- *     workspace `ws` of `ws_bytes` bytes (see gini_workspace_size).  A fresh
+ *     workspace `ws` of `ws_bytes` bytes (see gini_workspace_size), 256-byte
+ *     aligned (as cudaMalloc returns; GINI_EINVAL otherwise).  A fresh
  *     workspace must be zero-filled once before first use.
  *   - Work is enqueued on `stream` (a cudaStream_t passed as void*; NULL is
  *     the legacy default stream) and runs asynchronously.  Argument errors are

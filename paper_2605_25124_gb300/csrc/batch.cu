@@ -496,6 +496,7 @@ extern "C" int gini_fit_batched(const gini_problem* probs, int nprob, const doub
                                 double* final_stress_dev, int* tuned_rows, void* ws,
                                 size_t ws_bytes, void* stream) {
   if (!probs || !nu_host || !Y0_dev || !Y_dev || !ws) return GINI_EINVAL;
+  if (ws_misaligned(ws)) return GINI_EINVAL;
   if (nprob < 1 || n_nu < 1 || n_nu > 8 || restarts < 1 || restarts > BATCH_RMAX || iters < 0)
     return GINI_EINVAL;
   if (!(eta0 > 0.0) || !isfinite(eta0)) return GINI_EINVAL;

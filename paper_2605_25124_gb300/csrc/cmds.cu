@@ -356,6 +356,7 @@ extern "C" int gini_classical_mds(const void* delta_dev, int64_t n, int layout, 
                                   uint64_t seed, float* Y_dev, double* eigvals_dev, void* ws,
                                   size_t ws_bytes, void* stream) {
   if (!delta_dev || !Y_dev || !eigvals_dev || !ws) return GINI_EINVAL;
+  if (ws_misaligned(ws)) return GINI_EINVAL;
   if (n < 2 || n > ((int64_t)1 << 31) || k < 1 || k > CMDS_KMAX || k > n || iters < 1)
     return GINI_EINVAL;
   if (layout == GINI_LAYOUT_FULL) {

@@ -83,4 +83,9 @@ __device__ __forceinline__ float bf16_bits_to_float(uint32_t h16) {
   return __uint_as_float(h16 << 16);
 }
 
+// Workspaces are 256-byte aligned (cudaMalloc's guarantee): the carved
+// regions are 256-byte multiples from the start, so every region keeps the
+// alignment bulk copies and vector loads need.
+inline bool ws_misaligned(const void* ws) { return (reinterpret_cast<uintptr_t>(ws) & 255) != 0; }
+
 }  // namespace gini

@@ -252,6 +252,7 @@ extern "C" int gini_dist(const float* X_dev, int64_t n, int64_t p, int64_t ldx,
                          int64_t ldd, int64_t nu_stride, double* sum_delta2_dev, void* ws,
                          size_t ws_bytes, void* stream) {
   if (!X_dev || !delta_dev || !nu_host || !ws) return GINI_EINVAL;
+  if (ws_misaligned(ws)) return GINI_EINVAL;
   if (n < 2 || p < 1 || p > 1024 || ldx < p || n_nu < 1 || n_nu > NU_MAX) return GINI_EINVAL;
   if (n > (int64_t)65535 * DIST_WARPS) return GINI_EINVAL;  // grid.y = ceil(n / 8)
   for (int q = 0; q < n_nu; ++q)

@@ -559,6 +559,7 @@ extern "C" int gini_neighbour_scores(const float* X_dev, int64_t n, int64_t p, i
                                      void* stream) {
   int st = check_xy(X_dev, n, p, ldx, Y_dev, k);
   if (st != GINI_OK || !out_dev || !ws) return GINI_EINVAL;
+  if (ws_misaligned(ws)) return GINI_EINVAL;
   if (k_trust < 0 || k_nn < 0 || k_trust > EVAL_KMAX || k_nn > EVAL_KMAX) return GINI_EINVAL;
   if (k_trust >= n || k_nn >= n || (k_nn > 0 && !labels_dev)) return GINI_EINVAL;
   if (k_trust > 0 && 2 * n - 3 * k_trust - 1 <= 0) return GINI_EINVAL;
@@ -593,6 +594,7 @@ extern "C" int gini_silhouette(const float* Y_dev, int64_t n, int k, const int* 
   if (!Y_dev || !labels_dev || !out_dev || !ws || n < 2 || k < 1 || k > 8 || n_labels < 1 ||
       n_labels > EVAL_CMAX)
     return GINI_EINVAL;
+  if (ws_misaligned(ws)) return GINI_EINVAL;
   if (ws_bytes < gini_eval_workspace_size(n, n_labels, 0)) return GINI_ENOMEM;
   cudaStream_t s = (cudaStream_t)stream;
   char* base = reinterpret_cast<char*>(ws);
@@ -622,6 +624,7 @@ extern "C" int gini_distance_correlations(const float* X_dev, int64_t n, int64_t
                                           void* stream) {
   int st = check_xy(X_dev, n, p, ldx, Y_dev, k);
   if (st != GINI_OK || !out_dev || !ws) return GINI_EINVAL;
+  if (ws_misaligned(ws)) return GINI_EINVAL;
   if (n > 65535) return GINI_EINVAL;  // pair indices and counts stay below 2^31
   const CorrLayout L = corr_layout(n, spearman != 0);
   if (ws_bytes < L.total) return GINI_ENOMEM;

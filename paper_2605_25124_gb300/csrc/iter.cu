@@ -1040,6 +1040,7 @@ extern "C" int gini_stress_grad_ex(const float* Y_dev, int64_t n, int k, double 
                                    double* stress_dev, float* grad_dev, void* ws, size_t ws_bytes,
                                    void* stream) {
   if (!Y_dev || !stress_dev || !ws) return GINI_EINVAL;
+  if (ws_misaligned(ws)) return GINI_EINVAL;  // point pairs are bulk-copied from it
   if (metric != GINI_METRIC_GINI && metric != GINI_METRIC_EUCLID) return GINI_EINVAL;
   if (loss != GINI_LOSS_KRUSKAL && loss != GINI_LOSS_SAMMON) return GINI_EINVAL;
   int st = check_common(n, k, nu, delta_dev, layout, dtype, ldd, col_scale_dev, norm);
@@ -1076,6 +1077,7 @@ extern "C" int gini_stress_grad(const float* Y_dev, int64_t n, int k, double nu,
 
 extern "C" int gini_mds_fit(const gini_fit_args* a, void* ws, size_t ws_bytes, void* stream) {
   if (!a || !ws || !a->Y_dev) return GINI_EINVAL;
+  if (ws_misaligned(ws)) return GINI_EINVAL;
   int st = check_common(a->n, a->k, a->nu, a->delta_dev, a->layout, a->dtype, a->ldd,
                         a->col_scale_dev, a->sum_delta2);
   if (st != GINI_OK) return st;

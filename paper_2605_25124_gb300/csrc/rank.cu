@@ -80,6 +80,7 @@ extern "C" int gini_rank(const float* v_dev, int64_t nseg, int64_t m, int64_t ld
   if (nseg < 0 || m < 1 || m > 1024 || ld < m) return GINI_EINVAL;
   if (nseg == 0) return GINI_OK;  // nothing to rank; pointers may be null
   if (!v_dev || !rank2_dev || !ws) return GINI_EINVAL;
+  if (ws_misaligned(ws)) return GINI_EINVAL;
   if (ws_bytes < gini_workspace_size(GINI_OP_RANK, nseg, m, 0, 0)) return GINI_ENOMEM;
   if (nseg > ((int64_t)1 << 34)) return GINI_EINVAL;  // grid size limit
   cudaStream_t s = (cudaStream_t)stream;

@@ -190,6 +190,7 @@ extern "C" int gini_nu_search(const float* X_dev, int64_t n, int64_t p, int64_t 
   if (!X_dev || !nu_host || !Y0_dev || !ks_dev || !mean_ks_dev || !best_dev || !Y_dev || !ws)
     return GINI_EINVAL;
   if (ldx < p) return GINI_EINVAL;
+  if (ws_misaligned(ws)) return GINI_EINVAL;
   SearchPlan pl;
   int st = plan_search(n, p, fold_host, K, n_nu, restarts, iters, pl);
   if (st != GINI_OK) return st;

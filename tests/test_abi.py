@@ -95,3 +95,26 @@ def test_host_side_validation(L):
     assert L.gini_mds_fit(ctypes.byref(a), ws, 1 << 20, None) == EINVAL
     a.iters, a.sum_delta2 = 5, 0.0
     assert L.gini_mds_fit(ctypes.byref(a), ws, 1 << 20, None) == EDEG
+
+
+def test_misaligned_workspace_is_rejected_on_the_host(L):
+    # fake device addresses: every call must return EINVAL before it touches them
+    from paper_2605_25124_gb300 import _lib
+    EINVAL = _lib.GINI_EINVAL
+    data, ws = 0x10000000, 0x20000010  # ws 16-byte but not 256-byte aligned
+    big = 1 << 40
+    nu = (ctypes.c_double * 1)(2.0)
+    assert L.gini_dist(data, 100, 8, 8, nu, 1, 1, 0, data, 0, 0, None, ws, big, None) == EINVAL
+    assert L.gini_rank(data, 10, 8, 8, data, ws, big, None) == EINVAL
+    assert L.gini_stress_grad(data, 100, 2, 2.0, data, 1, 0, 0, None, 1.0, data, data, ws, big,
+                              None) == EINVAL
+    args = _lib.FitArgs()
+    args.n, args.k, args.nu, args.delta_dev = 100, 2, 2.0, data
+    args.layout, args.dtype, args.sum_delta2, args.eta, args.iters = 1, 0, 1.0, 0.1, 5
+    args.Y_dev = data
+    assert L.gini_mds_fit(ctypes.byref(args), ws, big, None) == EINVAL
+    assert L.gini_classical_mds(data, 100, 1, 0, 0, None, 2, 5, 0, data, data, ws, big,
+                                None) == EINVAL
+    assert L.gini_distance_correlations(data, 100, 4, 4, data, 2, 1, data, ws, big,
+                                        None) == EINVAL
+    assert L.gini_silhouette(data, 100, 2, data, 2, data, ws, big, None) == EINVAL
