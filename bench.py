@@ -359,6 +359,24 @@ def _plain_and_variants(G, X, Y0, n, k, nu, T, stream, chosen_final, P):
                           "not_worse_than_plain_1e-4": float(fv) <= f * (1 + 1e-4),
                           "speedup_vs_plain": round(it / itv, 3)}
         del Dv
+    # a k = 3 embedding on the same Delta (tiled FP32; the generic fused kernel)
+    from paper_2605_25124_gb300 import workloads as wl
+    Dt = G.gini_pack(D, "f32")
+    Y3 = torch.from_numpy(wl.y_init(n, 3, seed=4242)).to(Y0.device)
+    eta3 = G.default_step(n, 3, nu, D.sum_delta2, 1.0)
+    G.gini_mds_fit(Y3, nu, Dt, eta3, 5, history=False, check_errors=False)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    _, _, f3 = G.gini_mds_fit(Y3, nu, Dt, eta3, T, history=False, check_errors=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    it3 = e0.elapsed_time(e1) / (T + 1)
+    variants["k3_f32"] = {"iter_ms": round(it3, 5), "iters_per_s": round(1e3 / it3, 1),
+                          "achieved_gbs": round(P * 4.0 / (it3 / 1e3) / 1e9, 1),
+                          "pairs_per_s": float(f"{P / (it3 / 1e3):.4e}"),
+                          "final_stress": float(f3)}
+    del Dt
     del mats, D
     torch.cuda.empty_cache()
     return plain, variants

@@ -159,6 +159,38 @@ __device__ __forceinline__ float pair_k(const float* yi, const float* yj, const 
   return d;
 }
 
+// Exact sign of (hi_i - hi_j) + (lo_i - lo_j) for TwoSum pairs, as -1, 0 or 1
+// on the FMA pipe: a = fma(dh, 2^64, dl) has the sign that decides (dl cannot
+// outweigh a non-zero dh; a = dl when dh = 0), and the scalings take any
+// non-zero value, subnormals included, to >= 1 before the saturations.
+__device__ __forceinline__ float exact_sign(float2 pi, float2 pj) {
+  const float dh = pi.x - pj.x, dl = pi.y - pj.y;
+  const float b = fmaf(dh, 0x1p64f, dl) * 0x1p126f;
+  return __saturatef(b * 0x1p24f) - __saturatef(-b * 0x1p24f);
+}
+
+// k = 3: with the midrank offsets x_c = R_c - 2 in {0, +-1/2, +-1} (from the
+// three exact pairwise signs) the table value (3/2) W(R_c) is an odd function
+// of x_c, so T(x) = x (A + B x^2) with T(1) = w[4] and T(1/2) = w[3] -- exact
+// at ties too, and no table lookups.
+template <>
+__device__ __forceinline__ float pair_k<3>(const float* yi, const float* yj, const float2* Pi,
+                                           const float2* Pj, const float* w, float (&dw)[3]) {
+  const float s01 = exact_sign(Pi[0], Pj[0]);  // sign(z_0 - z_1)
+  const float s02 = exact_sign(Pi[1], Pj[1]);
+  const float s12 = exact_sign(Pi[2], Pj[2]);
+  const float t1 = w[4], th = w[3];
+  const float A = (8.f * th - t1) * (1.f / 3.f), B = (4.f * t1 - 8.f * th) * (1.f / 3.f);
+  const float x[3] = {0.5f * (s01 + s02), 0.5f * (s12 - s01), -0.5f * (s02 + s12)};
+  float d = 0.f;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    dw[c] = x[c] * fmaf(B, x[c] * x[c], A);
+    d = fmaf(yi[c] - yj[c], dw[c], d);
+  }
+  return d;
+}
+
 // ------------------------------------------------------------ plain form ---
 
 // One warp per row i.  FWD: S over j > i.  !FWD: h_i over all j != i.
@@ -631,7 +663,9 @@ struct FusedKSmem {
   float colh[TILE][K];
 };
 
-template <int K, int DT, bool GRAD>
+// GK: Gini metric and Kruskal loss only (the other branches compiled out, so the
+// unrolled body stays small enough for the instruction cache).
+template <int K, int DT, bool GRAD, bool GK>
 __global__ void __launch_bounds__(FUSED_THREADS) k_fusedk(const IterParams Q, int64_t ntiles) {
   constexpr int NP = K * (K - 1) / 2;
   extern __shared__ __align__(16) unsigned char s_raw[];
@@ -674,43 +708,118 @@ __global__ void __launch_bounds__(FUSED_THREADS) k_fusedk(const IterParams Q, in
 #pragma unroll
       for (int a = 0; a < K; ++a) colacc[c][a] = 0.f;
     float S = 0.f;
-    for (int rr = 0; rr < 16; ++rr) {
-      const int rl = warp * 16 + rr;
+    // one pair of the tile: stress term, and dd/dy weighted by the loss into the
+    // row accumulator (racc) and, negated, the column accumulator
+    auto pair_terms = [&](int rl, int c, const float (&dl)[4], float (&racc)[K]) {
+      const int cl = 4 * lane + c;
       const int64_t gi = i0 + rl;
-      float dl[4];
-      load4<DT>(Q, tbase + (int64_t)rl * TILE + 4 * lane, dl, sc);
-      float racc[K];
+      const bool ok = gi < Q.n && j0 + cl < Q.n && (I != J || rl < cl);
+      float dw[K];
+      const float d = (!GK && Q.metric == GINI_METRIC_EUCLID)
+                          ? pair_euclid<K>(s_y[0][rl], s_y[1][cl], dw)
+                          : pair_k<K>(s_y[0][rl], s_y[1][cl], s_p[0][rl], s_p[1][cl], s_w, dw);
+      float sterm, gw;
+      loss_terms(GK ? GINI_LOSS_KRUSKAL : Q.loss, d, dl[c], sterm, gw);
+      sterm = ok ? sterm : 0.f;
+      gw = ok ? gw : 0.f;
+      S += sterm;
 #pragma unroll
-      for (int a = 0; a < K; ++a) racc[a] = 0.f;
+      for (int a = 0; a < K; ++a) {
+        const float tt = gw * dw[a];
+        racc[a] += tt;
+        colacc[c][a] -= tt;
+      }
+    };
+    // the same with the row's and the column's points already in registers
+    auto pair_terms_r = [&](int rl, int c, const float (&dl)[4], const float (&ry)[K],
+                            const float2 (&rp)[NP], const float (&cy)[K],
+                            const float2 (&cpp)[NP], float (&racc)[K]) {
+      const int cl = 4 * lane + c;
+      const int64_t gi = i0 + rl;
+      const bool ok = gi < Q.n && j0 + cl < Q.n && (I != J || rl < cl);
+      float dw[K];
+      const float d = (!GK && Q.metric == GINI_METRIC_EUCLID) ? pair_euclid<K>(ry, cy, dw)
+                                                              : pair_k<K>(ry, cy, rp, cpp, s_w, dw);
+      float sterm, gw;
+      loss_terms(GK ? GINI_LOSS_KRUSKAL : Q.loss, d, dl[c], sterm, gw);
+      sterm = ok ? sterm : 0.f;
+      gw = ok ? gw : 0.f;
+      S += sterm;
+#pragma unroll
+      for (int a = 0; a < K; ++a) {
+        const float tt = gw * dw[a];
+        racc[a] += tt;
+        colacc[c][a] -= tt;
+      }
+    };
+    if constexpr (K <= 4) {
+      // the lane's 4 columns in registers for the whole tile, a row's points
+      // once per row; rows in blocks of 8: per-row partials stay in registers
+      // and one 3-stage transpose-reduction (reduce8) per component serves 8 rows
+      float cy[4][K];
+      float2 cp[4][NP];
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
-        const int cl = 4 * lane + c;
-        const bool ok = gi < Q.n && j0 + cl < Q.n && (I != J || rl < cl);
-        float dw[K];
-        const float d = (Q.metric == GINI_METRIC_EUCLID)
-                            ? pair_euclid<K>(s_y[0][rl], s_y[1][cl], dw)
-                            : pair_k<K>(s_y[0][rl], s_y[1][cl], s_p[0][rl], s_p[1][cl], s_w, dw);
-        float sterm, gw;
-        loss_terms(Q.loss, d, dl[c], sterm, gw);
-        sterm = ok ? sterm : 0.f;
-        gw = ok ? gw : 0.f;
-        S += sterm;
 #pragma unroll
-        for (int a = 0; a < K; ++a) {
-          const float tt = gw * dw[a];
-          racc[a] += tt;
-          colacc[c][a] -= tt;
+        for (int a = 0; a < K; ++a) cy[c][a] = s_y[1][4 * lane + c][a];
+#pragma unroll
+        for (int q = 0; q < NP; ++q) cp[c][q] = s_p[1][4 * lane + c][q];
+      }
+      for (int rb = 0; rb < 16; rb += 8) {
+        float racc8[K][8];
+#pragma unroll
+        for (int a = 0; a < K; ++a)
+#pragma unroll
+          for (int q = 0; q < 8; ++q) racc8[a][q] = 0.f;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int rl = warp * 16 + rb + q;
+          float dl[4];
+          load4<DT>(Q, tbase + (int64_t)rl * TILE + 4 * lane, dl, sc);
+          float racc[K], ry[K];
+          float2 rp[NP];
+#pragma unroll
+          for (int a = 0; a < K; ++a) {
+            racc[a] = 0.f;
+            ry[a] = s_y[0][rl][a];
+          }
+#pragma unroll
+          for (int qq = 0; qq < NP; ++qq) rp[qq] = s_p[0][rl][qq];
+#pragma unroll
+          for (int c = 0; c < 4; ++c) pair_terms_r(rl, c, dl, ry, rp, cy[c], cp[c], racc);
+#pragma unroll
+          for (int a = 0; a < K; ++a) racc8[a][q] = racc[a];
+        }
+        if (GRAD) {
+#pragma unroll
+          for (int a = 0; a < K; ++a) {
+            const float v = reduce8(racc8[a], lane);
+            const int64_t gi = i0 + warp * 16 + rb + rev3(lane & 7);
+            if (lane < 8 && gi < Q.n) atomicAdd(Q.h + gi * K + a, v);
+          }
         }
       }
-      if (GRAD) {
+    } else {
+      for (int rr = 0; rr < 16; ++rr) {
+        const int rl = warp * 16 + rr;
+        const int64_t gi = i0 + rl;
+        float dl[4];
+        load4<DT>(Q, tbase + (int64_t)rl * TILE + 4 * lane, dl, sc);
+        float racc[K];
 #pragma unroll
-        for (int a = 0; a < K; ++a) {
+        for (int a = 0; a < K; ++a) racc[a] = 0.f;
 #pragma unroll
-          for (int o = 16; o >= 1; o >>= 1) racc[a] += __shfl_xor_sync(FULL_MASK, racc[a], o);
+        for (int c = 0; c < 4; ++c) pair_terms(rl, c, dl, racc);
+        if (GRAD) {
+#pragma unroll
+          for (int a = 0; a < K; ++a) {
+#pragma unroll
+            for (int o = 16; o >= 1; o >>= 1) racc[a] += __shfl_xor_sync(FULL_MASK, racc[a], o);
+          }
+          if (lane == 0 && gi < Q.n)
+#pragma unroll
+            for (int a = 0; a < K; ++a) atomicAdd(Q.h + gi * K + a, racc[a]);
         }
-        if (lane == 0 && gi < Q.n)
-#pragma unroll
-          for (int a = 0; a < K; ++a) atomicAdd(Q.h + gi * K + a, racc[a]);
       }
     }
     Sd += (double)S;
@@ -939,14 +1048,14 @@ static void full_k(int k, const IterParams& Q, cudaStream_t s) {
   }
 }
 
-template <int K, int DT, bool GRAD>
+template <int K, int DT, bool GRAD, bool GK = false>
 static void launch_fusedk(unsigned g, const IterParams& Q, int64_t ntiles, cudaStream_t s) {
   const size_t smem = sizeof(FusedKSmem<K>);
   if (smem + 1024 > 48 * 1024)  // plus the kernel's static shared memory
-    cudaFuncSetAttribute(k_fusedk<K, DT, GRAD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_fusedk<K, DT, GRAD, GK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
   gini_count_launch(1);
-  k_fusedk<K, DT, GRAD><<<g, FUSED_THREADS, smem, s>>>(Q, ntiles);
+  k_fusedk<K, DT, GRAD, GK><<<g, FUSED_THREADS, smem, s>>>(Q, ntiles);
 }
 
 template <int DT, bool GRAD>
@@ -957,7 +1066,12 @@ static void launch_fused_dt(int k, const IterParams& Q, cudaStream_t s) {
   if (!scalar2_path(k, Q.metric, Q.loss)) {
     switch (k) {
       case 2: launch_fusedk<2, DT, GRAD>(g, Q, ntiles, s); return;
-      case 3: launch_fusedk<3, DT, GRAD>(g, Q, ntiles, s); return;
+      case 3:
+        if (Q.metric == GINI_METRIC_GINI && Q.loss == GINI_LOSS_KRUSKAL)
+          launch_fusedk<3, DT, GRAD, true>(g, Q, ntiles, s);
+        else
+          launch_fusedk<3, DT, GRAD>(g, Q, ntiles, s);
+        return;
       case 4: launch_fusedk<4, DT, GRAD>(g, Q, ntiles, s); return;
       case 5: launch_fusedk<5, DT, GRAD>(g, Q, ntiles, s); return;
       case 6: launch_fusedk<6, DT, GRAD>(g, Q, ntiles, s); return;
