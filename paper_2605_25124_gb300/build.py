@@ -48,8 +48,20 @@ def _fingerprint() -> str:
 
 
 def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
-    """Compile if sources changed since the last build; returns the .so path."""
+    """Compile if sources changed since the last build; returns the .so path.
+    Processes that build at once (one per GPU) take turns on a file lock; the
+    later ones find the stamp current and return."""
+    import fcntl
     os.makedirs(OUT_DIR, exist_ok=True)
+    with open(os.path.join(OUT_DIR, ".lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        try:
+            return _build_locked(force, verbose, ptxas_info)
+        finally:
+            fcntl.flock(lock, fcntl.LOCK_UN)
+
+
+def _build_locked(force: bool, verbose: bool, ptxas_info: bool) -> str:
     stamp = os.path.join(OUT_DIR, "stamp")
     fp = _fingerprint()
     if not force and os.path.exists(LIB) and os.path.exists(stamp):
