@@ -681,7 +681,17 @@ __global__ void __launch_bounds__(FUSED_THREADS) k_fusedk(const IterParams Q, in
   double Sd = 0.0;
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     __syncthreads();
-    if (threadIdx.x == 0) tile_decode(t, Q.tiles, s_ij[0], s_ij[1]);
+    if (threadIdx.x == 0) {
+      tile_decode(t, Q.tiles, s_ij[0], s_ij[1]);
+      // this CTA's next tile is one contiguous block: have it in L2 by then
+      const int64_t tn = t + gridDim.x;
+      if (tn < ntiles) {
+        constexpr unsigned esz = DT == GINI_F32 ? 4 : (DT == GINI_FP8E4M3 ? 1 : 2);
+        const char* base = reinterpret_cast<const char*>(Q.delta) + tn * (int64_t)(TILE * TILE) * esz;
+        bulk_prefetch_l2(base, TILE * TILE * esz);
+        if (DT == GINI_BF16X2) bulk_prefetch_l2(base + Q.plane * esz, TILE * TILE * esz);
+      }
+    }
     __syncthreads();
     const int I = s_ij[0], J = s_ij[1];
     const int64_t i0 = (int64_t)I * TILE, j0 = (int64_t)J * TILE;
