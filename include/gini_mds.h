@@ -419,6 +419,14 @@ int gini_distance_correlations(const float* X_dev, int64_t n, int64_t p, int64_t
                                const float* Y_dev, int k, int spearman, double* out_dev, void* ws,
                                size_t ws_bytes, void* stream);
 
+/* Diagnostics (no counterpart in the paper): runs the bounded wait that the
+ * pipelined kernels use for their bulk copies on a barrier that nothing
+ * completes.  After limit_ns (1e3 .. 1e9 ns) the wait gives up and records
+ * GINI_ETIMEOUT in ws, which the next gini_check returns; the context stays
+ * usable.  It shows that an expired wait ends the kernel instead of hanging
+ * the GPU.  ws: at least 256 bytes. */
+int gini_selftest_wait_timeout(uint64_t limit_ns, void* ws, size_t ws_bytes, void* stream);
+
 /* A step size for gini_mds_fit: eta0 times the inverse of a Gershgorin bound
  * on the Gauss-Newton curvature of S,
  *   eta = eta0 * sum_delta2 / (2 (n-1) k ((k/2) w_max)^2),  w_max = ((k-1)/k)^{nu-1}.

@@ -78,6 +78,7 @@ SIGNATURES = {
                                    _vp]),
     "gini_distance_correlations": (_c.c_int, [_vp, _i64, _i64, _i64, _vp, _c.c_int, _c.c_int,
                                               _vp, _vp, _c.c_size_t, _vp]),
+    "gini_selftest_wait_timeout": (_c.c_int, [_c.c_uint64, _vp, _c.c_size_t, _vp]),
     "gini_cmds_workspace_size": (_c.c_size_t, [_i64, _c.c_int]),
     "gini_classical_mds": (_c.c_int, [_vp, _i64, _c.c_int, _c.c_int, _i64, _vp, _c.c_int,
                                       _c.c_int, _c.c_uint64, _vp, _vp, _vp, _c.c_size_t, _vp]),

@@ -56,15 +56,16 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 }
 
 // Waits for the barrier phase with the given parity to complete.  Returns
-// false if *abort becomes non-zero or WAIT_LIMIT_NS passes first.
+// false if *abort becomes non-zero or limit_ns passes first.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
-                                                  const volatile int* abort) {
+                                                  const volatile int* abort,
+                                                  uint64_t limit_ns = WAIT_LIMIT_NS) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = globaltimer_ns();
   for (;;) {
     if (mbar_try_wait(bar, parity)) return true;
     if (abort && *abort) return false;
-    if (globaltimer_ns() - t0 > WAIT_LIMIT_NS) return false;
+    if (globaltimer_ns() - t0 > limit_ns) return false;
   }
 }
 

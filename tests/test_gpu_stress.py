@@ -155,3 +155,29 @@ def test_nonfinite_embedding_reported(G):
     Y[5, 1] = np.nan
     with pytest.raises(GiniError, match="ENONFINITE"):
         G.gini_stress_grad(torch.from_numpy(Y).cuda(), 2.0, _dis(G, D, n, "f32", sd2))
+
+
+def test_bounded_wait_expires_and_context_survives(G):
+    # the pipelined kernels' bounded wait, on a barrier nothing completes: it
+    # must give up after its limit, report ETIMEOUT through gini_check, and
+    # leave the GPU usable for the next call
+    import time
+    from paper_2605_25124_gb300 import _lib
+    L = _lib.lib()
+    ws = torch.zeros(4096, dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    assert L.gini_selftest_wait_timeout(20_000_000, ws.data_ptr(), ws.numel(), None) == 0
+    st = L.gini_check(ws.data_ptr(), None)
+    dt = time.perf_counter() - t0
+    assert st == _lib.GINI_ETIMEOUT
+    assert 0.015 <= dt < 5.0
+    assert L.gini_check(ws.data_ptr(), None) == 0  # the check cleared it
+    assert L.gini_selftest_wait_timeout(10, ws.data_ptr(), ws.numel(), None) == _lib.GINI_EINVAL
+    n = 60
+    _, D, sd2 = _ref_delta(n, 5, 2.0, seed=260)
+    Y = wl.y_init(n, 2, seed=261)
+    S, _ = G.gini_stress_grad(torch.from_numpy(Y).cuda(), 2.0, _dis(G, D, n, "f32", sd2))
+    Dq = quantize(D, "f32")
+    Sref, _ = orc.stress_grad(Y.astype(np.float64), 2.0, np.triu(Dq, 1) + np.triu(Dq, 1).T, sd2)
+    assert float(S) == pytest.approx(Sref, rel=1e-5)
