@@ -64,6 +64,25 @@ __device__ __forceinline__ void store_delta(const DistParams& P, int q, int64_t 
   }
 }
 
+// Order-preserving 32-bit image of a float (ascending as unsigned integers)
+// and its inverse.
+__device__ __forceinline__ unsigned ord_bits(float f) {
+  const unsigned b = __float_as_uint(f);
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float unord_bits(unsigned k) {
+  return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+
+// a + c as the TwoSum pair (hi, lo), hi = fl(a + c), hi + lo = a + c exactly;
+// -0 is replaced by +0 in both parts so equal values have equal bits.
+__device__ __forceinline__ float2 two_sum_canonical(float a, float c) {
+  const float hi = __fadd_rn(a, c);
+  const float bb = __fsub_rn(hi, a);
+  const float lo = __fadd_rn(__fsub_rn(a, __fsub_rn(hi, bb)), __fsub_rn(c, bb));
+  return make_float2(__fadd_rn(hi, 0.f), __fadd_rn(lo, 0.f));
+}
+
 // Skewed shared-memory address of table entry idx: sorted positions of one
 // lane are E apart, so idx ~ 2*E*ls + 2t; adding idx / (2E) spreads the lanes
 // of a segment over distinct banks.
@@ -116,42 +135,64 @@ k_dist(const DistParams P) {
     const int64_t j = jb + seg;
     const bool active = row_ok && j > i && j < P.n;
     if (!__any_sync(FULL_MASK, active)) continue;
-    float v[E];
-#pragma unroll
-    for (int t = 0; t < E; ++t) {
-      const int e = t * L + ls;
-      float xj = (active && e < m) ? __ldg(P.X + j * P.ldx + e) : 0.f;
-      v[t] = (e < m) ? s_xi[warp][e] - xj : __int_as_float(0x7f800000);  // pad with +inf
-    }
-    seg_bitonic_sort<E, L>(v, ls);
-
     float acc[NQ];
 #pragma unroll
     for (int q = 0; q < NQ; ++q) acc[q] = 0.f;
     const int pos0 = E * ls;
-    if (AFFINE) {
-      // nu = 2: (d/2) W(R) = R - (d+1)/2 at position pos (0-based): pos - (d-1)/2
+    if constexpr (AFFINE) {
+      // nu = 2: (d/2) W(R) = R - (d+1)/2 at position pos (0-based): pos - (d-1)/2.
+      // The weights are affine in the position, so the order of equal FP32
+      // differences does not change the sum: FP32 keys suffice.
+      float v[E];
+#pragma unroll
+      for (int t = 0; t < E; ++t) {
+        const int e = t * L + ls;
+        float xj = (active && e < m) ? __ldg(P.X + j * P.ldx + e) : 0.f;
+        v[t] = (e < m) ? s_xi[warp][e] - xj : __int_as_float(0x7f800000);  // pad with +inf
+      }
+      seg_bitonic_sort<E, L>(v, ls);
 #pragma unroll
       for (int t = 0; t < E; ++t) {
         const int pos = pos0 + t;
         if (pos < m) acc[0] = fmaf(v[t], (float)pos - mid, acc[0]);
       }
     } else {
+      // Weights that are not affine in the rank: the order must be that of the
+      // exact differences.  Each difference is the TwoSum pair (hi, lo),
+      // hi + lo = x_i - x_j exactly, ordered lexicographically through one
+      // 64-bit key; distinct differences that round to the same FP32 value stay
+      // distinct, equal keys are exact ties.  The sum uses hi.
+      unsigned long long kv[E];
+#pragma unroll
+      for (int t = 0; t < E; ++t) {
+        const int e = t * L + ls;
+        if (e < m) {
+          const float a = s_xi[warp][e];
+          const float c = active ? -__ldg(P.X + j * P.ldx + e) : 0.f;
+          const float2 hl = two_sum_canonical(a, c);
+          kv[t] = ((unsigned long long)ord_bits(hl.x) << 32) | ord_bits(hl.y);
+        } else {
+          kv[t] = ~0ull;  // padding above every real key
+        }
+      }
+      seg_bitonic_sort<E, L>(kv, ls);
       int run_lo[E];
       int carry_e;
       bool cont_right;
-      seg_runs<E, L>(v, ls, [](float a, float b) { return a == b; }, run_lo, carry_e, cont_right);
+      seg_runs<E, L>(kv, ls, [](unsigned long long a, unsigned long long b) { return a == b; },
+                     run_lo, carry_e, cont_right);
       int e = cont_right ? carry_e : pos0 + E - 1;
 #pragma unroll
       for (int t = E - 1; t >= 0; --t) {
-        if (t < E - 1) e = (v[t] == v[t + 1]) ? e : pos0 + t;
+        if (t < E - 1) e = (kv[t] == kv[t + 1]) ? e : pos0 + t;
         if (pos0 + t < m) {
-          // a value equal to the +inf padding (an overflowed difference) would
-          // extend its run into the padding: keep the run end inside [0, m)
+          const float hi = unord_bits((unsigned)(kv[t] >> 32));
+          // keep the run end inside [0, m) (padding keys are never equal to
+          // a real key, but the clamp costs nothing)
           const int a = tab_addr<E>(run_lo[t] + min(e, m - 1));
 #pragma unroll
           for (int q = 0; q < NQ; ++q)
-            if (q < P.n_nu) acc[q] = fmaf(v[t], s_tab[q * tab_stride + a], acc[q]);
+            if (q < P.n_nu) acc[q] = fmaf(hi, s_tab[q * tab_stride + a], acc[q]);
         }
       }
     }

@@ -150,3 +150,30 @@ def test_delta_two_points_worked_example(G):
     mats, sd2 = G.gini_dist(torch.from_numpy(X).cuda(), [2.0, 1.5, 3.0])
     for q, nu in enumerate([2.0, 1.5, 3.0]):
         assert mats[q].data[0, 1].item() == pytest.approx(1188 * 2.0 ** (1 - nu), rel=1e-6)
+
+
+@pytest.mark.parametrize("nus", [[1.3], [1.3, 2.0, 3.7]])
+def test_delta_exact_order_of_colliding_differences(G, nus):
+    # 1 - 2^-25 rounds to 1.0f: in the pair (0, 1) it meets an exact 1.0 at the
+    # top of the order, where W is steepest for nu < 2.  The two differences are
+    # distinct, so their ranks must differ as in the exact (oracle) order.
+    rng = np.random.default_rng(5000)
+    n, p = 24, 40
+    X = rng.standard_normal((n, p)).astype(np.float32)
+    X[0, :2] = [1.0, 1.0]
+    X[1, :2] = [2.0 ** -25, 0.0]
+    X[0, 2:] = rng.uniform(-0.5, 0.5, p - 2).astype(np.float32)
+    X[1, 2:] = rng.uniform(-0.5, 0.5, p - 2).astype(np.float32)
+    z = X[0].astype(np.float32) - X[1].astype(np.float32)
+    assert z[0] == z[1] == 1.0  # the collision really happens in FP32
+    D, sd2 = orc.delta(X, nus)
+    mats, s2 = G.gini_dist(torch.from_numpy(X).cuda(), nus, layout="full")
+    for v in range(len(nus)):
+        got = mats[v].data.cpu().numpy().astype(np.float64)
+        assert abs(got[0, 1] - D[v][0, 1]) <= 1e-6 * abs(D[v][0, 1]), (nus[v], got[0, 1], D[v][0, 1])
+        assert np.max(np.abs(got - D[v])) <= 1e-5 * np.abs(D[v]).max()
+        assert s2[v].item() == pytest.approx(sd2[v], rel=1e-6)
+    tm, _ = G.gini_dist(torch.from_numpy(X).cuda(), nus, layout="tiled", dtype="f32")
+    for v in range(len(nus)):
+        got = untile(tm[v].data.cpu().numpy(), n)
+        assert abs(got[0, 1] - D[v][0, 1]) <= 1e-6 * abs(D[v][0, 1])

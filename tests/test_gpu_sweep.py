@@ -1,0 +1,90 @@
+"""A seeded sweep of awkward sizes against the oracle: Delta for p across the
+sort's segment boundaries and ragged n, several nu from one sort, every
+layout/storage; stress and gradient for every k and storage form."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import gini_oracle as orc
+from paper_2605_25124_gb300 import workloads as wl
+from util import ENTRY_TOL, host_col_scale, quantize, tile_pack, untile
+
+pytestmark = pytest.mark.gpu
+
+P_EDGES = [1, 2, 3, 4, 5, 7, 8, 9, 15, 16, 17, 31, 32, 33, 63, 64, 65, 127, 128, 129, 255, 256,
+           257, 511, 512, 513, 700, 1023, 1024]
+
+
+def _dist_cases():
+    rng = np.random.default_rng(4040)
+    cases = []
+    for i, p in enumerate(P_EDGES):
+        n = int(rng.choice([2, 3, 5, 17, 64, 129, 200, 257]))
+        n_nu = int(rng.integers(1, 9))
+        nus = sorted(set(np.round(rng.uniform(1.05, 5.0, n_nu), 3)))
+        if i % 5 == 0:
+            nus = [2.0]  # the positional-weight path
+        cases.append((n, p, [float(v) for v in nus], ["gauss", "ties"][i % 2], i))
+    return cases
+
+
+def _X(data, n, p, seed):
+    if data == "ties":
+        return wl.integer_valued(n, p, seed=seed, levels=3)
+    return wl.gaussian_outliers(n, p, seed=seed)
+
+
+@pytest.mark.parametrize("n,p,nus,data,i", _dist_cases())
+def test_delta_sweep(G, n, p, nus, data, i):
+    X = _X(data, n, p, 4100 + i)
+    Dref, sref = orc.delta(X, nus)
+    Xd = torch.from_numpy(X).cuda()
+    mats, sd2 = G.gini_dist(Xd, nus, layout="full")
+    for v in range(len(nus)):
+        got = mats[v].data.cpu().numpy().astype(np.float64)
+        scale = max(np.abs(Dref[v]).max(), 1e-30)
+        assert np.max(np.abs(got - Dref[v])) <= 1e-5 * scale, (v, nus[v])
+        assert sd2[v].item() == pytest.approx(sref[v], rel=1e-5, abs=1e-30)
+    # tiled storage of the same matrices
+    tmats, _ = G.gini_dist(Xd, nus, layout="tiled", dtype="bf16x2")
+    for v in range(len(nus)):
+        t = tmats[v].data.view(torch.int16).cpu().numpy().view(np.uint16).astype(np.uint32)
+        vals = (t << 16).view(np.float32).astype(np.float64)
+        got = untile(vals, n, planes=2)
+        want = np.triu(Dref[v], 1)
+        assert np.max(np.abs(got - want)) <= ENTRY_TOL["bf16x2"] * max(np.abs(want).max(), 1e-30)
+
+
+def _stress_cases():
+    rng = np.random.default_rng(4200)
+    cases = []
+    for i in range(20):
+        n = int(rng.choice([2, 3, 4, 127, 128, 129, 255, 256, 300]))
+        k = int(rng.integers(2, 9))
+        nu = float(np.round(rng.uniform(1.1, 4.5), 2))
+        form = ["full", "f32", "bf16", "bf16x2", "fp8"][i % 5]
+        cases.append((n, k, nu, form, i))
+    return cases
+
+
+@pytest.mark.parametrize("n,k,nu,form,i", _stress_cases())
+def test_stress_grad_sweep(G, n, k, nu, form, i):
+    X = wl.gaussian_outliers(n, 6, seed=4300 + i)
+    D, sd2 = orc.delta(X, [nu])
+    D, sd2 = D[0], float(sd2[0])
+    if sd2 == 0.0:
+        pytest.skip("degenerate")
+    if form == "full":
+        Dd = G.Dissimilarity(torch.from_numpy(D.astype(np.float32)).cuda(), n, "full", "f32", sd2)
+        Dq = quantize(D, "f32")
+    else:
+        sc = host_col_scale(D) if form == "fp8" else None
+        Dd = G.Dissimilarity(torch.from_numpy(tile_pack(D, n, form, sc)).cuda(), n, "tiled", form,
+                             sd2, torch.from_numpy(sc).cuda() if sc is not None else None)
+        Dq = quantize(D, form, sc)
+    Dq = np.triu(Dq, 1) + np.triu(Dq, 1).T
+    Y = wl.y_init(n, k, seed=4400 + i, sd=1.0)
+    Sref, gref = orc.stress_grad(Y.astype(np.float64), nu, Dq, sd2)
+    S, g = G.gini_stress_grad(torch.from_numpy(Y).cuda(), nu, Dd)
+    assert float(S) == pytest.approx(Sref, rel=1e-5, abs=1e-12)
+    assert np.max(np.abs(g.cpu().numpy() - gref)) <= 1e-5 * max(np.abs(gref).max(), 1e-30)
