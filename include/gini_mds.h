@@ -151,8 +151,12 @@ int gini_rank(const float* v_dev, int64_t nseg, int64_t m, int64_t ld, int32_t* 
  *   ldd        leading dimension of a FULL matrix (>= n); ignored for TILED
  *   sum_delta2_dev  n_nu doubles out: sum_{i<j} delta_ij^2 (FP32 values,
  *              FP64 sum), or NULL
- * The differences x_i - x_j are formed in FP32 and ranked exactly as FP32
- * values.  Non-finite X is reported as GINI_ENONFINITE by gini_check. */
+ * The differences x_i - x_j are ranked in their exact order: each is the FP32
+ * TwoSum pair (hi, lo), hi + lo = x_i - x_j, compared lexicographically (two
+ * differences that round to one FP32 value are not a tie); the sums use hi.
+ * For a single nu = 2 the weights are affine in the rank and FP32 keys give
+ * the same result, so that case sorts FP32 values (about ten times faster).
+ * Non-finite X is reported as GINI_ENONFINITE by gini_check. */
 int gini_dist(const float* X_dev, int64_t n, int64_t p, int64_t ldx, const double* nu_host,
               int n_nu, int layout, int dtype, void* delta_dev, int64_t ldd, int64_t nu_stride,
               double* sum_delta2_dev, void* ws, size_t ws_bytes, void* stream);

@@ -2,13 +2,15 @@
 // (Section III-B, symmetrized generalized Gini pseudo-distance; Algorithm 1).
 //
 // Per pair (i, j), i < j, one segment of L lanes:
-//   z = x_i - x_j                         (FP32, E registers per lane)
-//   sort z ascending                      (register bitonic network)
+//   z = x_i - x_j as the TwoSum pair (hi, lo)   (E registers per lane)
+//   sort z ascending in its exact order          (register sorting network on
+//                                                 64-bit (hi, lo) keys)
 //   2R(pos) = first + last position of pos's tie run, + 2   (midranks)
-//   delta_q = sum_pos z(pos) * T_q[2R - 2],  T_q = (d/2) W_{d,nu_q}
+//   delta_q = sum_pos hi(pos) * T_q[2R - 2],  T_q = (d/2) W_{d,nu_q}
 // One sort serves every nu.  For a single nu = 2 the weight is affine in the
-// rank, (d/2) W = R - (d+1)/2, so a tie run's midrank weight equals the mean of
-// its positional weights and the run bookkeeping is skipped (exactly equal).
+// rank, (d/2) W = R - (d+1)/2: a tie run's midrank weight equals the mean of its
+// positional weights, and equal FP32 values give the same sum in any order, so
+// that case sorts the FP32 values and skips the run bookkeeping.
 //
 // Work split: CTA = 8 warps = 8 consecutive rows i; blockIdx.x picks a block
 // of CB columns j.  A warp keeps x_i in shared memory (in registers it would
