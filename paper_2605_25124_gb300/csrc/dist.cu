@@ -17,6 +17,7 @@
 // cost the 32 registers that let two CTAs share an SM) and walks its columns,
 // each of the 32/L segments taking every (32/L)-th j.  X is read through L2 (a
 // row is a few KB; the per-pair compute dwarfs the traffic).
+#include <float.h>
 #include <math.h>
 #include <stdio.h>
 
@@ -93,7 +94,9 @@ __device__ __forceinline__ int tab_addr(int idx) {
   return idx + (idx / (2 * E));
 }
 
-template <int E, int L, bool AFFINE>
+// TL, TR (affine path): registers t < TL hold a real element in every lane
+// (t*L + ls < m), registers t >= TR none.
+template <int E, int L, bool AFFINE, int TL = E, int TR = E>
 __global__ void __launch_bounds__(DIST_WARPS * 32)
 k_dist(const DistParams P) {
   constexpr int G = 32 / L;
@@ -118,21 +121,42 @@ k_dist(const DistParams P) {
     __syncthreads();
   }
 
+  // Affine path: sorted-position weights of the alternating layout, per
+  // (segment lane, register), zero at padding; rows padded to E + 4 floats so
+  // that the 16-byte reads of a quarter-warp fall in distinct banks.
+  __shared__ __align__(16) float s_cw[AFFINE ? L : 1][AFFINE ? E + 4 : 4];
+  if constexpr (AFFINE) {
+    // padding of odd lanes (negated, so at the bottom of the sorted sequence)
+    int n_lo = 0;
+    if (L >= 2)
+      for (int l = 1; l < L; l += 2) n_lo += E - min(E, m > l ? (m - l + L - 1) / L : 0);
+    const float mid = 0.5f * (float)(m - 1);
+    for (int idx = threadIdx.x; idx < L * E; idx += blockDim.x) {
+      const int l = idx / E, t = idx % E;
+      const bool odd = L >= 2 && (l & 1);
+      const int pos = E * l + (odd ? E - 1 - t : t) - n_lo;  // rank among real elements
+      s_cw[l][t] = (pos >= 0 && pos < m) ? (odd ? -1.f : 1.f) * ((float)pos - mid) : 0.f;
+    }
+  }
+
   const int64_t i = row0 + warp;
   const bool row_ok = i < P.n - 1;
   __shared__ float s_xi[DIST_WARPS][E * L];
 #pragma unroll
   for (int t = 0; t < E; ++t) {
     const int e = t * L + ls;
-    if (seg == 0) s_xi[warp][e] = (row_ok && e < m) ? __ldg(P.X + i * P.ldx + e) : 0.f;
+    float x = (row_ok && e < m) ? __ldg(P.X + i * P.ldx + e) : 0.f;
+    // affine path: stored with the sign of the lanes that read it (e and ls
+    // have the same parity when L is even)
+    if (AFFINE && L >= 2 && (e & 1)) x = -x;
+    if (seg == 0) s_xi[warp][e] = x;
   }
-  __syncwarp();
+  if constexpr (AFFINE) __syncthreads(); else __syncwarp();
 
   double sd2[NQ];
 #pragma unroll
   for (int q = 0; q < NQ; ++q) sd2[q] = 0.0;
 
-  const float mid = 0.5f * (float)(m - 1);
   for (int64_t jb = col0; jb < col0 + P.cb; jb += G) {
     const int64_t j = jb + seg;
     const bool active = row_ok && j > i && j < P.n;
@@ -142,22 +166,33 @@ k_dist(const DistParams P) {
     for (int q = 0; q < NQ; ++q) acc[q] = 0.f;
     const int pos0 = E * ls;
     if constexpr (AFFINE) {
-      // nu = 2: (d/2) W(R) = R - (d+1)/2 at position pos (0-based): pos - (d-1)/2.
-      // The weights are affine in the position, so the order of equal FP32
-      // differences does not change the sum: FP32 keys suffice.
-      float v[E];
+      // nu = 2: (d/2) W(R) = R - (d+1)/2 is affine in the rank, so the order
+      // of equal FP32 differences does not change the sum: FP32 keys suffice.
+      // u = s0 (x_i - x_j) with the lane's sign s0 (alternating layout),
+      // padded with FLT_MAX (weight 0; a real difference equal to it would
+      // carry the same value in whichever slot it lands).
+      const float nsg = (L >= 2 && (ls & 1)) ? 1.f : -1.f;  // -s0
+      float u[E];
 #pragma unroll
       for (int t = 0; t < E; ++t) {
         const int e = t * L + ls;
-        float xj = (active && e < m) ? __ldg(P.X + j * P.ldx + e) : 0.f;
-        v[t] = (e < m) ? s_xi[warp][e] - xj : __int_as_float(0x7f800000);  // pad with +inf
+        if (t < TR) {
+          const bool real = t < TL || e < m;
+          const float xj = (active && real) ? __ldg(P.X + j * P.ldx + e) : 0.f;
+          u[t] = real ? fmaf(nsg, xj, s_xi[warp][e]) : FLT_MAX;
+        } else {
+          u[t] = FLT_MAX;
+        }
       }
-      seg_bitonic_sort<E, L>(v, ls);
+      seg_sort_alternating<E, L, TR>(u, ls);
+      float2 acc2 = make_float2(0.f, 0.f);
 #pragma unroll
-      for (int t = 0; t < E; ++t) {
-        const int pos = pos0 + t;
-        if (pos < m) acc[0] = fmaf(v[t], (float)pos - mid, acc[0]);
+      for (int t = 0; t < E; t += 4) {
+        const float4 c = *reinterpret_cast<const float4*>(&s_cw[ls][t]);
+        acc2 = __ffma2_rn(make_float2(u[t], u[t + 1]), make_float2(c.x, c.y), acc2);
+        acc2 = __ffma2_rn(make_float2(u[t + 2], u[t + 3]), make_float2(c.z, c.w), acc2);
       }
+      acc[0] = acc2.x + acc2.y;
     } else {
       // Weights that are not affine in the rank: the order must be that of the
       // exact differences.  Each difference is the TwoSum pair (hi, lo),
@@ -249,7 +284,7 @@ __global__ void k_zero_diag(float* D, int64_t n, int64_t ldd, int64_t nu_stride,
     for (int q = 0; q < n_nu; ++q) D[(int64_t)q * nu_stride + i * ldd + i] = 0.f;
 }
 
-template <int E, int L, bool AFFINE>
+template <int E, int L, bool AFFINE, int TL = E, int TR = E>
 static cudaError_t launch_dist(const DistParams& P, cudaStream_t s) {
   const int m = (int)P.m;
   const int tab_n = 2 * m - 1;
@@ -257,7 +292,7 @@ static cudaError_t launch_dist(const DistParams& P, cudaStream_t s) {
   const size_t smem = AFFINE ? 0 : (size_t)P.n_nu * tab_stride * sizeof(float);
   // static (x_i rows) + dynamic (weight tables) may pass the 48 KB default
   if (smem > 0) {
-    cudaError_t e = cudaFuncSetAttribute(k_dist<E, L, AFFINE>,
+    cudaError_t e = cudaFuncSetAttribute(k_dist<E, L, AFFINE, TL, TR>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
@@ -266,22 +301,42 @@ static cudaError_t launch_dist(const DistParams& P, cudaStream_t s) {
   Q.cb = G * (L >= 8 ? 16 : 4);  // columns per CTA: several passes per warp
   dim3 grid((unsigned)((P.n + Q.cb - 1) / Q.cb), (unsigned)((P.n + DIST_WARPS - 1) / DIST_WARPS));
   gini_count_launch(1);
-  k_dist<E, L, AFFINE><<<grid, DIST_WARPS * 32, smem, s>>>(Q);
+  k_dist<E, L, AFFINE, TL, TR><<<grid, DIST_WARPS * 32, smem, s>>>(Q);
   return cudaGetLastError();
 }
 
-template <bool AFFINE>
-static cudaError_t dispatch_dist(const DistParams& P, cudaStream_t s) {
+// Generic keys (nu != 2): one instantiation per power-of-two segment size.
+static cudaError_t dispatch_dist_exact(const DistParams& P, cudaStream_t s) {
   const int64_t m = P.m;
-  if (m <= 4) return launch_dist<4, 1, AFFINE>(P, s);
-  if (m <= 8) return launch_dist<8, 1, AFFINE>(P, s);
-  if (m <= 16) return launch_dist<16, 1, AFFINE>(P, s);
-  if (m <= 32) return launch_dist<32, 1, AFFINE>(P, s);
-  if (m <= 64) return launch_dist<32, 2, AFFINE>(P, s);
-  if (m <= 128) return launch_dist<32, 4, AFFINE>(P, s);
-  if (m <= 256) return launch_dist<32, 8, AFFINE>(P, s);
-  if (m <= 512) return launch_dist<32, 16, AFFINE>(P, s);
-  return launch_dist<32, 32, AFFINE>(P, s);
+  if (m <= 4) return launch_dist<4, 1, false>(P, s);
+  if (m <= 8) return launch_dist<8, 1, false>(P, s);
+  if (m <= 16) return launch_dist<16, 1, false>(P, s);
+  if (m <= 32) return launch_dist<32, 1, false>(P, s);
+  if (m <= 64) return launch_dist<32, 2, false>(P, s);
+  if (m <= 128) return launch_dist<32, 4, false>(P, s);
+  if (m <= 256) return launch_dist<32, 8, false>(P, s);
+  if (m <= 512) return launch_dist<32, 16, false>(P, s);
+  return launch_dist<32, 32, false>(P, s);
+}
+
+// Affine (nu = 2): as above, with the bounds TL, TR on the real registers of
+// each segment size (m in (E*L/2, E*L] fills every register below E/2), and
+// the 32-lane segments split further by m so that the in-lane sort skips the
+// comparators of registers that only ever hold padding (m = 784: 25 of 32).
+static cudaError_t dispatch_dist_affine(const DistParams& P, cudaStream_t s) {
+  const int64_t m = P.m;
+  if (m <= 4) return launch_dist<4, 1, true, 1, 4>(P, s);
+  if (m <= 8) return launch_dist<8, 1, true, 4, 8>(P, s);
+  if (m <= 16) return launch_dist<16, 1, true, 8, 16>(P, s);
+  if (m <= 32) return launch_dist<32, 1, true, 16, 32>(P, s);
+  if (m <= 64) return launch_dist<32, 2, true, 16, 32>(P, s);
+  if (m <= 128) return launch_dist<32, 4, true, 16, 32>(P, s);
+  if (m <= 256) return launch_dist<32, 8, true, 16, 32>(P, s);
+  if (m <= 512) return launch_dist<32, 16, true, 16, 32>(P, s);
+  if (m <= 640) return launch_dist<32, 32, true, 16, 20>(P, s);
+  if (m <= 800) return launch_dist<32, 32, true, 20, 25>(P, s);
+  if (m <= 896) return launch_dist<32, 32, true, 25, 28>(P, s);
+  return launch_dist<32, 32, true, 28, 32>(P, s);
 }
 
 }  // namespace gini
@@ -352,7 +407,7 @@ extern "C" int gini_dist(const float* X_dev, int64_t n, int64_t p, int64_t ldx,
     P.layout = layout; P.dtype = dtype; P.out = delta_dev; P.ldd = ldd; P.nu_stride = nu_stride;
     P.tiles = tiles_1d(n); P.plane = gini_tiled_elems(n);
     P.sum_delta2 = sum_delta2_dev; P.err = err;
-    e = affine ? dispatch_dist<true>(P, s) : dispatch_dist<false>(P, s);
+    e = affine ? dispatch_dist_affine(P, s) : dispatch_dist_exact(P, s);
   }
   if (e != cudaSuccess) { gini_set_cuda_error(e); return GINI_ECUDA; }
   return GINI_OK;

@@ -69,14 +69,14 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   }
 }
 
-// Global -> shared bulk copy of `bytes` (multiple of 16, both addresses
-// 16-byte aligned) completing as transaction bytes on `bar`.
 // Asks for `bytes` (a multiple of 16, 16-byte aligned) of global memory to be
 // brought into L2 ahead of use; no completion to wait for.
 __device__ __forceinline__ void bulk_prefetch_l2(const void* src, unsigned bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }
 
+// Global -> shared bulk copy of `bytes` (multiple of 16, both addresses
+// 16-byte aligned) completing as transaction bytes on `bar`.
 __device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes,
                                               uint64_t* bar) {
   asm volatile(

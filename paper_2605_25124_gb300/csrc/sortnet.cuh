@@ -1,21 +1,23 @@
-// Register-resident bitonic sort of one segment spread over L lanes x E
+// Register-resident sorting networks for one segment spread over L lanes x E
 // registers, plus the tie-run (midrank) bookkeeping on the sorted segment.
 //
 // Layout: a segment is L consecutive lanes of a warp (L in 1..32, a power of
-// two, aligned); lane ls of the segment holds registers v[0..E).  The network
-// sorts the E*L values ascending so that afterwards position
-// pos = E*ls + t holds v[t] ("blocked" layout).  The initial placement of the
-// values is arbitrary: the caller loads them in whatever order is coalesced.
+// two, aligned); lane ls of the segment holds registers v[0..E).  Each lane
+// first sorts its own E registers; merge levels across lanes follow, each a
+// bitonic merge (a mirror stage, then half-cleaners at halving distances).
+// Partners closer than E positions sit in the same lane (register exchange);
+// farther ones in another lane of the segment, reached with a warp shuffle.
 //
-// Network (float keys): each lane first sorts its E registers with Batcher's
-// odd-even merge sort (fewer compare-exchanges than the bitonic levels it
-// replaces: 191 instead of 240 for E = 32); the levels across lanes follow.
-// Network (generic keys): the bitonic sorter written without direction flags.  For block size
-// kk = 2, 4, ..., E*L, element i is first compared with its mirror i ^ (kk-1)
-// inside the block, then with i ^ jj for jj = kk/4, ..., 1; the lower index
-// always keeps the minimum.  Partners closer than E positions sit in the same
-// lane (register exchange); farther ones in lane ls ^ (distance / E), reached
-// with a warp shuffle.
+// Generic keys (seg_bitonic_sort): the bitonic sorter written without
+// direction flags.  For block size kk = 2, 4, ..., E*L, element i is first
+// compared with its mirror i ^ (kk-1) inside the block, then with i ^ jj for
+// jj = kk/4, ..., 1; the lower index always keeps the minimum.  Afterwards
+// position E*ls + t holds v[t] ("blocked" layout).
+//
+// Float keys (seg_sort_alternating): the same merges on a layout in which
+// odd lanes hold negated values in reverse order, so that every exchange is
+// one minimum; the in-lane sort is Batcher's odd-even merge sort (191
+// compare-exchanges instead of 240 bitonic ones for E = 32).
 #pragma once
 
 #include "common.cuh"
@@ -38,23 +40,13 @@ __device__ __forceinline__ void cas(T& a, T& b) {
   b = hi;
 }
 
-// Cross-lane exchange: the lower lane keeps min(v, o), the upper max(v, o).
-// (Rewriting it as s * min(s*v, s*o), s = +-1, moves two of the three
-// operations off the ALU pipe but raised register use and measured slower.)
-__device__ __forceinline__ float keep_lo_hi(float v, float o, bool lower) {
-  return lower ? fminf(v, o) : fmaxf(v, o);
-}
+// Cross-lane exchange of generic keys: the lower lane keeps min(v, o), the
+// upper max(v, o).
 __device__ __forceinline__ unsigned long long keep_lo_hi(unsigned long long v,
                                                          unsigned long long o, bool lower) {
   return lower ? kmin(v, o) : kmax(v, o);
 }
 
-// Float keys: the cross-lane stages keep, in every lane whose role in the
-// stage is "upper" (keeps the maximum), the negated values.  Partners then have
-// opposite signs and both keep fminf(u, -o): the lower lane min(v, o), the upper
-// lane min(-v, -o) = -max(v, o).  One min per element on the ALU pipe instead of
-// a min, a max and a select; the sign changes between stages (a lane's role
-// depends on the stage's lane bit) are multiplications by +-1 on the FMA pipe.
 // Batcher's odd-even merge sort of N keys as a comparator list (compile time).
 template <int N>
 struct OemNet {
@@ -83,63 +75,96 @@ __device__ __forceinline__ void inlane_half_cleaners(float (&v)[E]) {
   }
 }
 
-// Cross-lane half-cleaners at lane distances D, D/2, ..., 1; sg is the sign
-// the lane's values carry on entry and on exit.
+// Multiplies every register by f (+-1) two at a time (packed f32x2, FMA pipe).
+template <int E>
+__device__ __forceinline__ void flip(float (&u)[E], float f) {
+  const float2 f2 = make_float2(f, f);
+#pragma unroll
+  for (int t = 0; t < E; t += 2) {
+    const float2 p = __fmul2_rn(make_float2(u[t], u[t + 1]), f2);
+    u[t] = p.x;
+    u[t + 1] = p.y;
+  }
+}
+
+// Cross-lane half-cleaners of the alternating layout (below) at lane
+// distances D, D/2, ..., 1; s is the sign the lane's values carry.  Lanes D
+// apart (D >= 2) have the same orientation, so register t meets register t;
+// lanes 1 apart have opposite orientations, so register t meets E-1-t.
 template <int E, int D>
-__device__ __forceinline__ void crosslane_half_cleaners(float (&v)[E], int ls, float& sg) {
+__device__ __forceinline__ void alt_half_cleaners(float (&u)[E], int ls, float& s) {
   if constexpr (D >= 1) {
     const float sn = (ls & D) == 0 ? 1.f : -1.f;
-    const float f = sn * sg;
-    sg = sn;
+    flip(u, sn * s);
+    s = sn;
+    if constexpr (D >= 2) {
 #pragma unroll
-    for (int t = 0; t < E; ++t) {
-      v[t] *= f;
-      const float o = __shfl_xor_sync(FULL_MASK, v[t], D);
-      v[t] = fminf(v[t], -o);
+      for (int t = 0; t < E; ++t) {
+        const float o = __shfl_xor_sync(FULL_MASK, u[t], D);
+        u[t] = fminf(u[t], -o);
+      }
+    } else {
+#pragma unroll
+      for (int t = 0; t < E / 2; ++t) {
+        const float a = __shfl_xor_sync(FULL_MASK, u[E - 1 - t], 1);
+        const float b = __shfl_xor_sync(FULL_MASK, u[t], 1);
+        u[t] = fminf(u[t], -a);
+        u[E - 1 - t] = fminf(u[E - 1 - t], -b);
+      }
     }
-    crosslane_half_cleaners<E, D / 2>(v, ls, sg);
+    alt_half_cleaners<E, D / 2>(u, ls, s);
   }
 }
 
-template <int E, int L, int KK>
-__device__ __forceinline__ void bitonic_level(float (&v)[E], int ls) {
-  if constexpr (KK <= E) {
-    if constexpr (KK == 2) {
-      constexpr OemNet<E> net{};
-#pragma unroll
-      for (int c = 0; c < net.n; ++c) cas(v[net.a[c]], v[net.b[c]]);
-    }
-  } else {
-    // mirror stage across lanes ls and ls ^ (KK/E - 1): register t meets the
-    // partner's register E-1-t
-    float sg = (ls & (KK / (2 * E))) == 0 ? 1.f : -1.f;
-#pragma unroll
-    for (int t = 0; t < E; ++t) v[t] *= sg;
-#pragma unroll
-    for (int t = 0; t < E / 2; ++t) {
-      const float a = __shfl_xor_sync(FULL_MASK, v[E - 1 - t], KK / E - 1);
-      const float b = __shfl_xor_sync(FULL_MASK, v[t], KK / E - 1);
-      v[t] = fminf(v[t], -a);
-      v[E - 1 - t] = fminf(v[E - 1 - t], -b);
-    }
-    crosslane_half_cleaners<E, KK / (4 * E)>(v, ls, sg);
-#pragma unroll
-    for (int t = 0; t < E; ++t) v[t] *= sg;
-    inlane_half_cleaners<E, E / 2>(v);
+// Merge level of K lanes (two sorted runs of K/2 lanes each become one).
+template <int E, int L, int K>
+__device__ __forceinline__ void alt_level(float (&u)[E], int ls, float s0) {
+  float s = s0;
+  if constexpr (K >= 4) {
+    // the lower run (lane bit K/2 clear) keeps the minima: it carries +v
+    const float sn = (ls & (K / 2)) == 0 ? 1.f : -1.f;
+    flip(u, sn * s);
+    s = sn;
   }
-  if constexpr (2 * KK <= E * L) bitonic_level<E, L, 2 * KK>(v, ls);
+  // First stage: position i of the block meets position K*E-1-i, which sits
+  // in lane ls ^ (K-1) -- of the other orientation -- at the same register.
+#pragma unroll
+  for (int t = 0; t < E; ++t) {
+    const float o = __shfl_xor_sync(FULL_MASK, u[t], K - 1);
+    u[t] = fminf(u[t], -o);
+  }
+  alt_half_cleaners<E, K / 4>(u, ls, s);  // ends with s = s0
+  inlane_half_cleaners<E, E / 2>(u);
+  if constexpr (2 * K <= L) alt_level<E, L, 2 * K>(u, ls, s0);
 }
 
-// Float keys: the cross-lane stages keep, in every lane whose role in the
-// stage is "upper" (keeps the maximum), the negated values.  Partners then have
-// opposite signs and both keep fminf(u, -o): the lower lane min(v, o), the upper
-// lane min(-v, -o) = -max(v, o).  One min per element on the ALU pipe instead of
-// a min, a max and a select; the sign changes between stages (a lane's role
-// depends on the stage's lane bit) are multiplications by +-1 on the FMA pipe.
-template <int E, int L>
-__device__ __forceinline__ void seg_bitonic_sort(float (&v)[E], int ls) {
+// Float keys in the alternating layout.  Lane ls of a segment holds
+// u = s0 * v, s0 = (-1)^(ls & 1), with its registers ascending in u: an even
+// lane holds sorted positions E*ls + t in register t, an odd lane holds
+// position E*ls + E-1-t in register t (negated values, reversed order).
+// In a cross-lane stage the lane that keeps the minima carries +v and its
+// partner -v, so both keep fminf(u, -o): min(v, o) in the first, and
+// min(-v, -o) = -max(v, o) in the second -- one ALU operation per element.
+// Within a lane a compare-exchange is a plain (min, max) on u.  A lane's sign
+// changes only when its role in the next stage differs (a multiplication by
+// -1 on the FMA pipe); the layout is the same at the end of every merge
+// level, so no level ends with a flip.
+//
+// The caller loads u already signed and pads with a value above every real
+// |u|, in registers TR..E-1 of every lane (and possibly lower ones): the
+// first, in-lane sort then skips every comparator touching a register at or
+// above TR, which would leave both values in place.  After the sort the
+// padding of even lanes sits at the top of the sequence and that of odd lanes
+// (negated) at the bottom.
+template <int E, int L, int TR>
+__device__ __forceinline__ void seg_sort_alternating(float (&u)[E], int ls) {
   static_assert((E & (E - 1)) == 0 && (L & (L - 1)) == 0 && L <= 32 && E >= 2, "powers of two");
-  bitonic_level<E, L, 2>(v, ls);
+  static_assert(TR >= 1 && TR <= E, "padding bound");
+  constexpr OemNet<E> net{};
+#pragma unroll
+  for (int c = 0; c < net.n; ++c)
+    if (net.b[c] < TR) cas(u[net.a[c]], u[net.b[c]]);
+  if constexpr (L >= 2) alt_level<E, L, 2>(u, ls, (ls & 1) ? -1.f : 1.f);
 }
 
 template <int E, int L, typename T>
