@@ -286,7 +286,11 @@ def run_ours(args, rank, local, world):
                      "frac": round(achieved_ops / alu_peak, 4),
                      "traffic": traffic.get("k_dist_bytes_per_launch"),
                      "peak_note": f"ALU pipe: {sms} SMs x 64 lanes x {max_mhz:.0f} MHz",
-                     "work_note": "per pair p*ceil(log2 p) comparisons (sorting lower bound)"},
+                     "work_note": "per pair p*ceil(log2 p) comparisons (sorting lower bound)",
+                     "alu_pipe_active_ncu": traffic.get("k_dist_alu_pipe_active"),
+                     "alu_pipe_note": "ALU-pipe utilisation of the same kernel from an ncu capture "
+                                      "(not a bench measurement): the network's own instruction "
+                                      "mix against the pipe's issue rate"},
         "iter_roofline": {"kernel": "k_fused2 (+ k_update) per iteration", "bound": "hbm",
                           "achieved": round(iter_gbs, 1), "peak": hbm_peak, "unit": "GB/s",
                           "frac": round(iter_gbs / hbm_peak, 4), "peak_source": peak_src,
