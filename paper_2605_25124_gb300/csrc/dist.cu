@@ -96,9 +96,8 @@ __device__ __forceinline__ int tab_addr(int idx) {
 
 // TL, TR (affine path): registers t < TL hold a real element in every lane
 // (t*L + ls < m), registers t >= TR none.
-template <int E, int L, bool AFFINE, int TL = E, int TR = E>
-__global__ void __launch_bounds__(DIST_WARPS * 32)
-k_dist(const DistParams P) {
+template <int E, int L, bool AFFINE, int TL, int TR>
+__device__ __forceinline__ void dist_body(const DistParams& P) {
   constexpr int G = 32 / L;
   constexpr int NQ = AFFINE ? 1 : NU_MAX;  // nu slots carried in registers
   extern __shared__ float s_tab[];  // n_nu x tab_stride
@@ -153,9 +152,18 @@ k_dist(const DistParams P) {
   }
   if constexpr (AFFINE) __syncthreads(); else __syncwarp();
 
-  double sd2[NQ];
-#pragma unroll
-  for (int q = 0; q < NQ; ++q) sd2[q] = 0.0;
+  // sum of delta^2 per nu: in registers for the affine path (one nu); in
+  // shared memory, one slot per segment, for the generic path, where eight
+  // FP64 registers held across the sort would cost its occupancy
+  constexpr int NR = AFFINE ? 1 : 0;
+  double sd2[NR > 0 ? NR : 1];
+  sd2[0] = 0.0;
+  __shared__ double s_sd2[AFFINE ? 1 : DIST_WARPS][AFFINE ? 1 : G][NU_MAX];
+  if constexpr (!AFFINE) {
+    for (int idx = threadIdx.x; idx < DIST_WARPS * G * NU_MAX; idx += blockDim.x)
+      (&s_sd2[0][0][0])[idx] = 0.0;
+    __syncthreads();
+  }
 
   for (int64_t jb = col0; jb < col0 + P.cb; jb += G) {
     const int64_t j = jb + seg;
@@ -213,23 +221,24 @@ k_dist(const DistParams P) {
         }
       }
       seg_bitonic_sort<E, L>(kv, ls);
-      int run_lo[E];
-      int carry_e;
+      // A tie run holds equal keys, so one hi: its members' terms sum to
+      // count * hi * T_q[first + last], added once at the run's last entry
+      // (in the lane that holds it; s is the run's first position).
       bool cont_right;
-      seg_runs<E, L>(kv, ls, [](unsigned long long a, unsigned long long b) { return a == b; },
-                     run_lo, carry_e, cont_right);
-      int e = cont_right ? carry_e : pos0 + E - 1;
+      int s = seg_first_run_start<E, L>(
+          kv, ls, [](unsigned long long a, unsigned long long b) { return a == b; }, cont_right);
 #pragma unroll
-      for (int t = E - 1; t >= 0; --t) {
-        if (t < E - 1) e = (kv[t] == kv[t + 1]) ? e : pos0 + t;
-        if (pos0 + t < m) {
+      for (int t = 0; t < E; ++t) {
+        if (t > 0 && kv[t] != kv[t - 1]) s = pos0 + t;
+        const bool last = (t < E - 1) ? (kv[t] != kv[t + 1]) : !cont_right;
+        const int pos = pos0 + t;
+        if (last && pos < m) {  // padding (positions >= m) forms runs of its own
           const float hi = unord_bits((unsigned)(kv[t] >> 32));
-          // keep the run end inside [0, m) (padding keys are never equal to
-          // a real key, but the clamp costs nothing)
-          const int a = tab_addr<E>(run_lo[t] + min(e, m - 1));
+          const float w = hi * (float)(pos - s + 1);
+          const int a = tab_addr<E>(s + pos);
 #pragma unroll
           for (int q = 0; q < NQ; ++q)
-            if (q < P.n_nu) acc[q] = fmaf(hi, s_tab[q * tab_stride + a], acc[q]);
+            if (q < P.n_nu) acc[q] = fmaf(w, s_tab[q * tab_stride + a], acc[q]);
         }
       }
     }
@@ -245,27 +254,44 @@ k_dist(const DistParams P) {
       for (int q = 0; q < NQ; ++q) {
         if (q < P.n_nu) {
           store_delta(P, q, i, j, acc[q]);
-          sd2[q] += (double)acc[q] * (double)acc[q];
+          const double d2 = (double)acc[q] * (double)acc[q];
+          if constexpr (AFFINE) sd2[0] += d2;
+          else s_sd2[warp][seg][q] += d2;
         }
       }
     }
   }
 
-  // sum_{i<j} delta^2: warp, then CTA, then one FP64 atomic per nu.
+  // sum_{i<j} delta^2: warp (or segment slots), then CTA, then one FP64
+  // atomic per nu.
+  if constexpr (AFFINE) {
 #pragma unroll
-  for (int q = 0; q < NQ; ++q) {
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) sd2[q] += __shfl_xor_sync(FULL_MASK, sd2[q], o);
+    for (int o = 16; o >= 1; o >>= 1) sd2[0] += __shfl_xor_sync(FULL_MASK, sd2[0], o);
+    if (lane == 0) s_red[warp][0] = sd2[0];
   }
-  if (lane == 0)
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) s_red[warp][q] = sd2[q];
   __syncthreads();
   if (threadIdx.x < P.n_nu && P.sum_delta2) {
     double s = 0.0;
-    for (int w = 0; w < DIST_WARPS; ++w) s += s_red[w][threadIdx.x];
+    for (int w = 0; w < DIST_WARPS; ++w) {
+      if constexpr (AFFINE) s += s_red[w][threadIdx.x];
+      else
+        for (int g = 0; g < G; ++g) s += s_sd2[w][g][threadIdx.x];
+    }
     if (s != 0.0) atomicAdd(P.sum_delta2 + threadIdx.x, s);
   }
+}
+
+// Entry points.  The affine kernel fits three CTAs per SM as compiled; the
+// generic one is bounded to two (128 registers, a few spilled) instead of the
+// one CTA its 64-bit network would otherwise take.
+template <int E, int L, int TL, int TR>
+__global__ void __launch_bounds__(DIST_WARPS * 32) k_dist(const DistParams P) {
+  dist_body<E, L, true, TL, TR>(P);
+}
+
+template <int E, int L>
+__global__ void __launch_bounds__(DIST_WARPS * 32, 2) k_dist_exact(const DistParams P) {
+  dist_body<E, L, false, E, E>(P);
 }
 
 __global__ void k_check_finite(const float* X, int64_t n, int64_t m, int64_t ld, unsigned* err) {
@@ -284,15 +310,22 @@ __global__ void k_zero_diag(float* D, int64_t n, int64_t ldd, int64_t nu_stride,
     for (int q = 0; q < n_nu; ++q) D[(int64_t)q * nu_stride + i * ldd + i] = 0.f;
 }
 
+template <int E, int L, bool AFFINE, int TL, int TR>
+static auto dist_kernel() {
+  if constexpr (AFFINE) return k_dist<E, L, TL, TR>;
+  else return k_dist_exact<E, L>;
+}
+
 template <int E, int L, bool AFFINE, int TL = E, int TR = E>
 static cudaError_t launch_dist(const DistParams& P, cudaStream_t s) {
+  void (*kern)(const DistParams) = dist_kernel<E, L, AFFINE, TL, TR>();
   const int m = (int)P.m;
   const int tab_n = 2 * m - 1;
   const int tab_stride = tab_n - 1 + (tab_n - 1) / (2 * E) + 1;
   const size_t smem = AFFINE ? 0 : (size_t)P.n_nu * tab_stride * sizeof(float);
   // static (x_i rows) + dynamic (weight tables) may pass the 48 KB default
   if (smem > 0) {
-    cudaError_t e = cudaFuncSetAttribute(k_dist<E, L, AFFINE, TL, TR>,
+    cudaError_t e = cudaFuncSetAttribute(kern,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
@@ -301,7 +334,7 @@ static cudaError_t launch_dist(const DistParams& P, cudaStream_t s) {
   Q.cb = G * (L >= 8 ? 16 : 4);  // columns per CTA: several passes per warp
   dim3 grid((unsigned)((P.n + Q.cb - 1) / Q.cb), (unsigned)((P.n + DIST_WARPS - 1) / DIST_WARPS));
   gini_count_launch(1);
-  k_dist<E, L, AFFINE, TL, TR><<<grid, DIST_WARPS * 32, smem, s>>>(Q);
+  kern<<<grid, DIST_WARPS * 32, smem, s>>>(Q);
   return cudaGetLastError();
 }
 

@@ -257,4 +257,33 @@ __device__ __forceinline__ void seg_runs(const T (&v)[E], int ls, KeyEq eq, int 
   for (int t = 1; t < E; ++t) run_lo[t] = eq(v[t], v[t - 1]) ? run_lo[t - 1] : pos0 + t;
 }
 
+// Start of the tie run holding the lane's first entry (its position in the
+// segment), by the same scan as seg_runs; cont_right as there.  Enough for
+// sums that take each run once, at its last entry.
+template <int E, int L, typename T, typename KeyEq>
+__device__ __forceinline__ int seg_first_run_start(const T (&v)[E], int ls, KeyEq eq,
+                                                   bool& cont_right) {
+  const int pos0 = E * ls;
+  T prev = __shfl_up_sync(FULL_MASK, v[E - 1], 1, L);
+  T next = __shfl_down_sync(FULL_MASK, v[0], 1, L);
+  const bool cont_left = (ls > 0) && eq(prev, v[0]);
+  cont_right = (ls < L - 1) && eq(v[E - 1], next);
+  int cnt_last = 0;
+  bool all_eq = true;
+#pragma unroll
+  for (int t = 0; t < E; ++t) {
+    cnt_last += eq(v[t], v[E - 1]) ? 1 : 0;
+    all_eq = all_eq && eq(v[t], v[0]);
+  }
+  // start of the run holding the lane's last entry (-1: began in an earlier lane)
+  int sl = (all_eq && cont_left) ? -1 : pos0 + E - cnt_last;
+#pragma unroll
+  for (int d = 1; d < L; d <<= 1) {
+    const int o = __shfl_up_sync(FULL_MASK, sl, d, L);
+    if (ls >= d && sl < 0) sl = o;
+  }
+  const int carry_s = __shfl_up_sync(FULL_MASK, sl, 1, L);
+  return cont_left ? carry_s : pos0;
+}
+
 }  // namespace gini
