@@ -106,8 +106,15 @@ __global__ void __launch_bounds__(TILE / ROWS * 32) k_batch_iter(const BatchPara
   constexpr int WARPS = TILE / ROWS;
   constexpr int NT = WARPS * 32;
   __shared__ float2 s_u[2][BATCH_RMAX][TILE];  // [rows | cols][restart][point]
-  __shared__ float s_col[WARPS][TILE];
-  __shared__ float s_S[WARPS];
+  // column and stress partials, double-buffered by restart parity where the
+  // static shared memory allows (8 warps): restart r + 1 fills the other
+  // buffer while restart r's is still being summed, so one barrier per restart
+  // suffices (restart r + 2 reuses a buffer only after every thread has passed
+  // restart r + 1's barrier, i.e. finished reading it).  16 warps: one buffer,
+  // a second barrier per restart.
+  constexpr int NBUF = WARPS <= 8 ? 2 : 1;
+  __shared__ float s_col[NBUF][WARPS][TILE];
+  __shared__ float s_S[NBUF][WARPS];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int R = B.restarts;
   const int64_t g_begin = B.total_tiles * blockIdx.x / gridDim.x;
@@ -202,7 +209,8 @@ __global__ void __launch_bounds__(TILE / ROWS * 32) k_batch_iter(const BatchPara
       // stress of this (fit, tile)
 #pragma unroll
       for (int o = 16; o >= 1; o >>= 1) S += __shfl_xor_sync(FULL_MASK, S, o);
-      if (lane == 0) s_S[warp] = S;
+      const int buf = NBUF == 2 ? (r & 1) : 0;
+      if (lane == 0) s_S[buf][warp] = S;
       if (GRAD) {
         const float rs = reduce_rows<ROWS>(rowv, lane);
         if (lane < ROWS) {
@@ -210,22 +218,22 @@ __global__ void __launch_bounds__(TILE / ROWS * 32) k_batch_iter(const BatchPara
           if (gi < n) atomicAdd(B.h + sg.h_off + r * n + gi, rs);
         }
 #pragma unroll
-        for (int c = 0; c < 4; ++c) s_col[warp][4 * lane + c] = col[c];
+        for (int c = 0; c < 4; ++c) s_col[buf][warp][4 * lane + c] = col[c];
       }
       __syncthreads();
       if (GRAD && threadIdx.x < TILE) {
         float v = 0.f;
 #pragma unroll
-        for (int w = 0; w < WARPS; ++w) v += s_col[w][threadIdx.x];
+        for (int w = 0; w < WARPS; ++w) v += s_col[buf][w][threadIdx.x];
         const int64_t gj = j0 + threadIdx.x;
         if (gj < n) atomicAdd(B.h + sg.h_off + r * n + gj, v);
       }
       if (threadIdx.x == 0) {
         float v = 0.f;
-        for (int w = 0; w < WARPS; ++w) v += s_S[w];
+        for (int w = 0; w < WARPS; ++w) v += s_S[buf][w];
         atomicAdd(B.acc + sg.fit0 + r, (double)v);
       }
-      __syncthreads();
+      if constexpr (NBUF == 1) __syncthreads();
     }
   }
 }
