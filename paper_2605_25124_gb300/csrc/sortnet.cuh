@@ -65,13 +65,13 @@ struct OemNet {
   }
 };
 
-template <int E, int JJ>
-__device__ __forceinline__ void inlane_half_cleaners(float (&v)[E]) {
+template <int E, int JJ, typename T>
+__device__ __forceinline__ void inlane_half_cleaners(T (&v)[E]) {
   if constexpr (JJ >= 1) {
 #pragma unroll
     for (int t = 0; t < E; ++t)
       if ((t ^ JJ) > t) cas(v[t], v[t ^ JJ]);
-    inlane_half_cleaners<E, JJ / 2>(v);
+    inlane_half_cleaners<E, JJ / 2, T>(v);
   }
 }
 
@@ -170,16 +170,30 @@ __device__ __forceinline__ void seg_sort_alternating(float (&u)[E], int ls) {
 template <int E, int L, typename T>
 __device__ __forceinline__ void seg_bitonic_sort(T (&v)[E], int ls) {
   static_assert((E & (E - 1)) == 0 && (L & (L - 1)) == 0 && L <= 32 && E >= 2, "powers of two");
+  // Block sizes up to E: within the lane, unrolled.
 #pragma unroll
-  for (int kk = 2; kk <= E * L; kk <<= 1) {
-    // mirror stage: i <-> i ^ (kk - 1)
-    if (kk <= E) {
+  for (int kk = 2; kk <= E; kk <<= 1) {
+#pragma unroll
+    for (int t = 0; t < E; ++t) {  // mirror stage: i <-> i ^ (kk - 1)
+      const int p = t ^ (kk - 1);
+      if (p > t) cas(v[t], v[p]);
+    }
+#pragma unroll
+    for (int jj = kk / 4; jj >= 1; jj >>= 1) {  // half-cleaners: i <-> i ^ jj
 #pragma unroll
       for (int t = 0; t < E; ++t) {
-        const int p = t ^ (kk - 1);
+        const int p = t ^ jj;
         if (p > t) cas(v[t], v[p]);
       }
-    } else {
+    }
+  }
+  // Larger blocks: the lane distances and roles are run-time values and every
+  // level ends with the same in-lane half-cleaners, so the levels and their
+  // cross-lane stages are loops -- one copy of the code instead of one per
+  // stage, which keeps the kernel inside the instruction cache.
+#pragma unroll 1
+  for (int kk = 2 * E; kk <= E * L; kk <<= 1) {
+    {
       const int mask = kk / E - 1;
       const bool lower = (ls & (kk / (2 * E))) == 0;
 #pragma unroll
@@ -191,25 +205,16 @@ __device__ __forceinline__ void seg_bitonic_sort(T (&v)[E], int ls) {
         v[E - 1 - t] = keep_lo_hi(v[E - 1 - t], b, lower);
       }
     }
-    // half-cleaners: i <-> i ^ jj
+#pragma unroll 1
+    for (int d = kk / (4 * E); d >= 1; d >>= 1) {  // half-cleaners at lane distance d
+      const bool lower = (ls & d) == 0;
 #pragma unroll
-    for (int jj = kk / 4; jj >= 1; jj >>= 1) {
-      if (jj >= E) {
-        const int mask = jj / E;
-        const bool lower = (ls & mask) == 0;
-#pragma unroll
-        for (int t = 0; t < E; ++t) {
-          T o = __shfl_xor_sync(FULL_MASK, v[t], mask);
-          v[t] = keep_lo_hi(v[t], o, lower);
-        }
-      } else {
-#pragma unroll
-        for (int t = 0; t < E; ++t) {
-          const int p = t ^ jj;
-          if (p > t) cas(v[t], v[p]);
-        }
+      for (int t = 0; t < E; ++t) {
+        T o = __shfl_xor_sync(FULL_MASK, v[t], d);
+        v[t] = keep_lo_hi(v[t], o, lower);
       }
     }
+    inlane_half_cleaners<E, E / 2, T>(v);
   }
 }
 
