@@ -153,6 +153,7 @@ __global__ void __launch_bounds__(TILE / ROWS * 32) k_batch_iter(const BatchPara
     const float2 k64 = make_float2(0x1p64f, 0x1p64f);
     const float2 k126 = make_float2(0x1p126f, 0x1p126f);
     const float2 m1 = make_float2(-1.f, -1.f);
+    const float2 k2 = make_float2(2.f, 2.f);
     const float2 nc2 = make_float2(-sg.c2, -sg.c2);
     for (int r = 0; r < R; ++r) {
       float rowv[ROWS];
@@ -180,11 +181,12 @@ __global__ void __launch_bounds__(TILE / ROWS * 32) k_batch_iter(const BatchPara
           const float2 s2 = __fadd2_rn(dh, dlo);
           // exact sign of u_i - u_j on the FMA pipe: dh dominates dlo unless it is
           // zero; the scalings take any nonzero value, subnormals included, to
-          // >= 1 so the saturations give 1 / 0 per side
+          // magnitude >= 2, so the saturating FMA gives 1, 1/2 or 0
           const float2 b2 = __fmul2_rn(__ffma2_rn(dh, k64, dlo), k126);
-          const float2 pp = make_float2(__saturatef(b2.x * 0x1p24f), __saturatef(b2.y * 0x1p24f));
-          const float2 qq = make_float2(__saturatef(-b2.x * 0x1p24f), __saturatef(-b2.y * 0x1p24f));
-          const float2 sig = __ffma2_rn(qq, m1, pp);
+          // sp = (sigma + 1) / 2 in {0, 1/2, 1}: one saturating FMA per column
+          const float2 sp = make_float2(__saturatef(fmaf(b2.x, 0x1p24f, 0.5f)),
+                                        __saturatef(fmaf(b2.y, 0x1p24f, 0.5f)));
+          const float2 sig = __ffma2_rn(sp, k2, m1);  // 2 sp - 1
           float2 rp = __ffma2_rn(nc2, __fmul2_rn(s2, sig), dv[p]);  // r' = delta - c2 |s|
           if (masked) {
             const int cl = 4 * lane + 2 * p;

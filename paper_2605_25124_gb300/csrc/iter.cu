@@ -434,7 +434,7 @@ __device__ __forceinline__ void load4_smem(const unsigned char* stage, int rr, i
 // sum, which needs -t, collects t' directly.
 //   sigma: a = fma(dh, 2^64, dl) has the sign of u_i - u_j (dl cannot
 //   outweigh a non-zero dh; a = dl exactly when dh = 0), and
-//   sat(a 2^150) - sat(-a 2^150) maps it to exactly -1, 0 or 1.
+//   sat(a 2^150 + 1/2) maps it to exactly 0, 1/2 or 1 = (sigma + 1) / 2.
 template <int DT, bool GRAD, bool MASKED>
 __device__ __forceinline__ void chunk_compute(const unsigned char* stage, int rbase, int lane,
                                               const float2 (&nuh)[2], const float2 (&nul)[2],
@@ -445,6 +445,7 @@ __device__ __forceinline__ void chunk_compute(const unsigned char* stage, int rb
   const float2 k64 = make_float2(0x1p64f, 0x1p64f);
   const float2 k126 = make_float2(0x1p126f, 0x1p126f);
   const float2 m1 = make_float2(-1.f, -1.f);
+  const float2 k2 = make_float2(2.f, 2.f);
   const float2 nc2 = make_float2(-c2, -c2);
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
@@ -460,9 +461,10 @@ __device__ __forceinline__ void chunk_compute(const unsigned char* stage, int rb
       const float2 dlo = __fadd2_rn(ul2, nul[p]);
       const float2 s2 = __fadd2_rn(dh, dlo);
       const float2 b2 = __fmul2_rn(__ffma2_rn(dh, k64, dlo), k126);
-      const float2 pp = make_float2(__saturatef(b2.x * 0x1p24f), __saturatef(b2.y * 0x1p24f));
-      const float2 qq = make_float2(__saturatef(-b2.x * 0x1p24f), __saturatef(-b2.y * 0x1p24f));
-      const float2 sig = __ffma2_rn(qq, m1, pp);
+      // sp = (sigma + 1) / 2 in {0, 1/2, 1}: one saturating FMA per column
+      const float2 sp = make_float2(__saturatef(fmaf(b2.x, 0x1p24f, 0.5f)),
+                                    __saturatef(fmaf(b2.y, 0x1p24f, 0.5f)));
+      const float2 sig = __ffma2_rn(sp, k2, m1);  // 2 sp - 1
       float2 rp = __ffma2_rn(nc2, __fmul2_rn(s2, sig), d2);  // r' = delta - c2 |s|
       if (MASKED) {
         const int rl = rl0 + q, cl = 4 * lane + 2 * p;
