@@ -23,6 +23,17 @@ def untile(flat, n, planes=1):
     return np.triu(out, 1)
 
 
+def tiled_flat_index(i, j, n):
+    """Flat index of entry (i, j), i < j, in the tiled upper-triangle layout:
+    tiles (I, J), I <= J, in row-major order of (I, J), each B x B row-major."""
+    i = np.asarray(i, dtype=np.int64)
+    j = np.asarray(j, dtype=np.int64)
+    T = -(-n // B)
+    I, J = i // B, j // B
+    t = I * T - I * (I - 1) // 2 + (J - I)
+    return t * B * B + (i % B) * B + (j % B)
+
+
 def rel_err(got, ref, floor=0.0):
     """max |got - ref| / max(|ref|, floor); entries equal on both sides count 0."""
     got = np.asarray(got, dtype=np.float64)
