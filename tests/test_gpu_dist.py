@@ -177,3 +177,25 @@ def test_delta_exact_order_of_colliding_differences(G, nus):
     for v in range(len(nus)):
         got = untile(tm[v].data.cpu().numpy(), n)
         assert abs(got[0, 1] - D[v][0, 1]) <= 1e-6 * abs(D[v][0, 1])
+
+
+@pytest.mark.parametrize("p", [5, 33, 784])
+@pytest.mark.parametrize("nus", [[2.0], [1.5, 3.0]])
+def test_delta_rows_differing_by_a_constant_vector_are_zero(G, p, nus):
+    # x_i - x_j = (c_i - c_j) * 1: every component ties, the midrank is (m+1)/2
+    # where W vanishes, so delta = 0 exactly (translation invariance); integer
+    # data keep the differences exact in FP32.  A fit on it is degenerate.
+    from paper_2605_25124_gb300._lib import GiniError
+    rng = np.random.default_rng(900 + p)
+    n = 70
+    base = rng.integers(-20, 20, p).astype(np.float32)
+    c = rng.integers(-50, 50, n).astype(np.float32)
+    X = base[None, :] + c[:, None]
+    mats, sd2 = G.gini_dist(torch.from_numpy(X).cuda(), nus, layout="full")
+    for v in range(len(nus)):
+        assert float(mats[v].data.abs().max()) == 0.0
+        assert float(sd2[v]) == 0.0
+    D = mats[0]
+    Y0 = torch.from_numpy(wl.y_init(n, 2, seed=901)).cuda()
+    with pytest.raises(GiniError, match="EDEGENERATE"):
+        G.gini_mds_fit(Y0, nus[0], D, 1.0, 3, history=False)
