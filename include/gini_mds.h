@@ -154,8 +154,9 @@ int gini_rank(const float* v_dev, int64_t nseg, int64_t m, int64_t ld, int32_t* 
  * The differences x_i - x_j are ranked in their exact order: each is the FP32
  * TwoSum pair (hi, lo), hi + lo = x_i - x_j, compared lexicographically (two
  * differences that round to one FP32 value are not a tie); the sums use hi.
- * For a single nu = 2 the weights are affine in the rank and FP32 keys give
- * the same result, so that case sorts FP32 values (about ten times faster).
+ * For a single nu = 2 or nu = 3 the weights are affine in the rank
+ * ((d/2) W_{d,3} = ((d-1)/d) (d/2) W_{d,2}) and FP32 keys give the same
+ * result, so those cases sort FP32 values (about six times faster).
  * Non-finite X is reported as GINI_ENONFINITE by gini_check. */
 int gini_dist(const float* X_dev, int64_t n, int64_t p, int64_t ldx, const double* nu_host,
               int n_nu, int layout, int dtype, void* delta_dev, int64_t ldd, int64_t nu_stride,

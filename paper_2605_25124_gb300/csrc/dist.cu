@@ -10,7 +10,8 @@
 // One sort serves every nu.  For a single nu = 2 the weight is affine in the
 // rank, (d/2) W = R - (d+1)/2: a tie run's midrank weight equals the mean of its
 // positional weights, and equal FP32 values give the same sum in any order, so
-// that case sorts the FP32 values and skips the run bookkeeping.
+// that case sorts the FP32 values and skips the run bookkeeping.  So does a
+// single nu = 3, whose weight is the same affine function times (d-1)/d.
 //
 // Work split: CTA = 8 warps = 8 consecutive rows i; blockIdx.x picks a block
 // of CB columns j.  A warp keeps x_i in shared memory (in registers it would
@@ -44,6 +45,7 @@ struct DistParams {
   double* sum_delta2;
   unsigned* err;
   int cb;             // columns per CTA
+  float affine_scale; // affine path: (d/2) W / (R - (d+1)/2), 1 for nu = 2, (d-1)/d for nu = 3
 };
 
 __device__ __forceinline__ void store_delta(const DistParams& P, int q, int64_t i, int64_t j,
@@ -200,7 +202,7 @@ __device__ __forceinline__ void dist_body(const DistParams& P) {
         acc2 = __ffma2_rn(make_float2(u[t], u[t + 1]), make_float2(c.x, c.y), acc2);
         acc2 = __ffma2_rn(make_float2(u[t + 2], u[t + 3]), make_float2(c.z, c.w), acc2);
       }
-      acc[0] = acc2.x + acc2.y;
+      acc[0] = (acc2.x + acc2.y) * P.affine_scale;
     } else {
       // Weights that are not affine in the rank: the order must be that of the
       // exact differences.  Each difference is the TwoSum pair (hi, lo),
@@ -403,7 +405,9 @@ extern "C" int gini_dist(const float* X_dev, int64_t n, int64_t p, int64_t ldx,
   cudaStream_t s = (cudaStream_t)stream;
   unsigned* err = reinterpret_cast<unsigned*>(ws);
   float* wtab = reinterpret_cast<float*>(reinterpret_cast<char*>(ws) + WS_HEADER);
-  const bool affine = (n_nu == 1 && nu_host[0] == 2.0);
+  // W_{d,nu} is affine in the rank for nu = 2 and nu = 3:
+  // (d/2) W_{d,3}(R) = ((d-1)/d) (R - (d+1)/2) = ((d-1)/d) (d/2) W_{d,2}(R)
+  const bool affine = (n_nu == 1 && (nu_host[0] == 2.0 || nu_host[0] == 3.0));
   const int tab_n = (int)(2 * p - 1);
   if (!affine) {
     // T_q[idx] = (d/2) W_{d,nu_q}((idx + 2)/2), W(R) = ((R-1)/d)^{nu-1} - ((d-R)/d)^{nu-1}
@@ -440,6 +444,7 @@ extern "C" int gini_dist(const float* X_dev, int64_t n, int64_t p, int64_t ldx,
     P.layout = layout; P.dtype = dtype; P.out = delta_dev; P.ldd = ldd; P.nu_stride = nu_stride;
     P.tiles = tiles_1d(n); P.plane = gini_tiled_elems(n);
     P.sum_delta2 = sum_delta2_dev; P.err = err;
+    P.affine_scale = (affine && nu_host[0] == 3.0) ? (float)((double)(p - 1) / (double)p) : 1.f;
     e = affine ? dispatch_dist_affine(P, s) : dispatch_dist_exact(P, s);
   }
   if (e != cudaSuccess) { gini_set_cuda_error(e); return GINI_ECUDA; }

@@ -40,9 +40,9 @@ def test_delta_full_f32_all_vector_lengths(G, p):
         assert sd2[q] == pytest.approx(sref[q], rel=1e-5)
 
 
-@pytest.mark.parametrize("nu", [2.0, 1.1, 4.5])
+@pytest.mark.parametrize("nu", [2.0, 3.0, 1.1, 4.5])
 def test_delta_single_nu_paths(G, nu):
-    # nu = 2 alone takes the positional-weight path; other nu the tie-run path.
+    # nu = 2 or 3 alone takes the positional-weight path; other nu the tie-run path.
     X = wl.image_like(30, seed=7)
     ref, sref = orc.delta(X, [nu])
     got, sd2 = _gpu_full(G, X, [nu])

@@ -55,7 +55,7 @@ def test_delta_sweep(G, n, p, nus, data, i):
         assert np.max(np.abs(got - want)) <= ENTRY_TOL["bf16x2"] * max(np.abs(want).max(), 1e-30)
 
 
-# nu = 2 alone: the alternating-layout network, at every boundary of its
+# nu = 2 or 3 alone: the alternating-layout network, at every boundary of its
 # dispatch (segment sizes and the padding bounds of 32-lane segments).
 P_AFFINE = [1, 2, 3, 4, 5, 8, 9, 16, 17, 32, 33, 64, 65, 128, 129, 256, 257, 512, 513, 600, 640,
             641, 700, 784, 799, 800, 801, 896, 897, 1000, 1023, 1024]
@@ -63,11 +63,12 @@ P_AFFINE = [1, 2, 3, 4, 5, 8, 9, 16, 17, 32, 33, 64, 65, 128, 129, 256, 257, 512
 
 @pytest.mark.parametrize("p", P_AFFINE)
 @pytest.mark.parametrize("data", ["gauss", "ties"])
-def test_delta_affine_sweep(G, p, data):
+@pytest.mark.parametrize("nu", [2.0, 3.0])
+def test_delta_affine_sweep(G, p, data, nu):
     n = 37 if p > 256 else 130
     X = _X(data, n, p, 4500 + p)
-    Dref, sref = orc.delta(X, [2.0])
-    mats, sd2 = G.gini_dist(torch.from_numpy(X).cuda(), [2.0], layout="full")
+    Dref, sref = orc.delta(X, [nu])
+    mats, sd2 = G.gini_dist(torch.from_numpy(X).cuda(), [nu], layout="full")
     got = mats[0].data.cpu().numpy().astype(np.float64)
     scale = max(np.abs(Dref[0]).max(), 1e-30)
     assert np.max(np.abs(got - Dref[0])) <= 1e-5 * scale

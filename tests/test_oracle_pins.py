@@ -98,6 +98,22 @@ def test_nu2_equals_half_pairwise_l1():
             assert orc.gini_dg(x, y) == pytest.approx(want, rel=1e-12, abs=1e-12)
 
 
+def test_nu3_is_the_nu2_distance_times_d_minus_1_over_d():
+    # W_{d,3}(R) = ((R-1)/d)^2 - ((d-R)/d)^2 = (2R - d - 1)(d - 1)/d^2 is
+    # affine in R, (d-1)/d times W_{d,2}: so at nu = 3
+    # Dbar = ((d-1)/d) * 1/2 sum_{a<b} |z_a - z_b|, ties or not.
+    rng = np.random.default_rng(5)
+    for d in (1, 2, 5, 13, 50):
+        for gen in ("cont", "ties"):
+            if gen == "cont":
+                x, y = rng.standard_normal(d), rng.standard_normal(d)
+            else:
+                x, y = rng.integers(0, 3, d).astype(float), rng.integers(0, 3, d).astype(float)
+            z = x - y
+            want = (d - 1) / d * 0.5 * np.abs(z[:, None] - z[None, :]).sum() / 2.0
+            assert orc.pd(x, y, 3.0) == pytest.approx(want, rel=1e-12, abs=1e-12)
+
+
 def test_general_nu_against_rank_weight_identity_with_ties():
     # With Fbar = 1 - R/d and R_{-z}(-z_j) = d + 1 - R_z(z_j) the two terms of
     # the symmetrization combine into (d/2) sum_j z_j W(R_j),
