@@ -89,3 +89,37 @@ def test_batched_graph_reuse_and_errors(G):
         G.gini_fit_batched(Xd, nus, 17, T, torch.zeros(17 * 290 * 2, device="cuda"))
     with pytest.raises(GiniError, match="EINVAL"):
         G.gini_fit_batched(Xd, [0.9], R, T, Y0)
+
+
+def test_batched_benchmark_configuration_sampled(G):
+    """The benchmark's batch (64 UCI-sized problems x 8 nu x 8 restarts, the
+    autotuned launch) for one iteration; the oracle rebuilds Delta for the
+    three smallest problems and the smallest integer-valued one and
+    checks S(Y0) and the first step of every nu and restart of those."""
+    w = wl.WORKLOADS["uci-batch-64"]
+    Xs = wl.uci_like_batch(w["n_problems"], w["seed"])
+    R, nus = w["restarts"], [float(v) for v in w["nu"]]
+    ns = [X.shape[0] for X in Xs]
+    Y0s = [wl.y_init(R * n, 2, seed=w["seed"] + 1000 + q) for q, n in enumerate(ns)]
+    Xd = [torch.from_numpy(X).cuda() for X in Xs]
+    Y0 = torch.from_numpy(np.concatenate([y.reshape(-1) for y in Y0s])).cuda()
+    out = G.gini_fit_batched(Xd, nus, R, 1, Y0, eta0=1.0, history=True)
+    Yb = out["Y"].cpu().numpy()
+    sl = _slices(ns, len(nus), R)
+    order = np.argsort(ns)
+    ints = [q for q in order if q % 4 == 3]
+    picks = sorted({int(q) for q in order[:3]} | {int(ints[0])})
+    for q in picks:
+        n = ns[q]
+        D, sd2 = orc.delta(Xs[q], nus)
+        for v, nu in enumerate(nus):
+            eta = orc.default_step(n, 2, nu, sd2[v], 1.0)
+            for r in range(R):
+                y0 = Y0s[q][r * n:(r + 1) * n].astype(np.float64)
+                y1, h = orc.fit(D[v], nu, sd2[v], y0, eta, 1)
+                assert out["history"][0, q, v, r].item() == pytest.approx(h[0], rel=1e-5)
+                a, b = sl[q, v, r]
+                step = Yb[a:b].reshape(n, 2) - y0
+                step_ref = y1 - y0
+                assert np.max(np.abs(step - step_ref)) <= (1e-5 * np.abs(step_ref).max()
+                                                          + 2e-7 * np.abs(y0).max()), (q, v, r)
