@@ -176,8 +176,9 @@ __device__ __forceinline__ void dist_body(const DistParams& P) {
     for (int q = 0; q < NQ; ++q) acc[q] = 0.f;
     const int pos0 = E * ls;
     if constexpr (AFFINE) {
-      // nu = 2: (d/2) W(R) = R - (d+1)/2 is affine in the rank, so the order
-      // of equal FP32 differences does not change the sum: FP32 keys suffice.
+      // nu = 2: (d/2) W(R) = R - (d+1)/2 is affine in the rank (nu = 3: the
+      // same times (d-1)/d, applied to the sum), so the order of equal FP32
+      // differences does not change the sum: FP32 keys suffice.
       // u = s0 (x_i - x_j) with the lane's sign s0 (alternating layout),
       // padded with FLT_MAX (weight 0; a real difference equal to it would
       // carry the same value in whichever slot it lands).
