@@ -334,7 +334,11 @@ static cudaError_t launch_dist(const DistParams& P, cudaStream_t s) {
   }
   DistParams Q = P;
   constexpr int G = 32 / L;
-  Q.cb = G * (L >= 8 ? 16 : 4);  // columns per CTA: several passes per warp
+  // Columns per CTA (several passes per warp): more of them amortise the CTA's
+  // setup (weight table, x_i rows) where the grid stays many waves deep --
+  // large n, or narrow segments with many pairs per warp.
+  const bool wide = P.n >= 8192 || L < 8;
+  Q.cb = G * (L >= 8 ? (wide ? 64 : 16) : (wide ? 16 : 4));
   dim3 grid((unsigned)((P.n + Q.cb - 1) / Q.cb), (unsigned)((P.n + DIST_WARPS - 1) / DIST_WARPS));
   gini_count_launch(1);
   kern<<<grid, DIST_WARPS * 32, smem, s>>>(Q);
