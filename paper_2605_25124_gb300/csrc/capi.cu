@@ -51,7 +51,7 @@ extern "C" size_t gini_workspace_size(int op, int64_t n, int64_t m, int k, int i
     case GINI_OP_RANK: return WS_HEADER;
     case GINI_OP_DIST: {
       const int64_t mm = m < 1 ? 1 : m;
-      return WS_HEADER + (size_t)8 * (size_t)(2 * mm - 1) * sizeof(float);
+      return WS_HEADER + 256 + (size_t)8 * (size_t)(2 * mm - 1) * sizeof(float);
     }
     case GINI_OP_STRESS: return gini_iter_ws_bytes(n, k < 2 ? 2 : k, 1);
     case GINI_OP_FIT: return gini_iter_ws_bytes(n, k < 2 ? 2 : k, (iters < 0 ? 0 : iters) + 1);

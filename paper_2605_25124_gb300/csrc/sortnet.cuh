@@ -264,13 +264,19 @@ __device__ __forceinline__ void seg_runs(const T (&v)[E], int ls, KeyEq eq, int 
 
 // Start of the tie run holding the lane's first entry (its position in the
 // segment), by the same scan as seg_runs; cont_right as there.  Enough for
-// sums that take each run once, at its last entry.
-template <int E, int L, typename T, typename KeyEq>
+// sums that take each run once, at its last entry.  ALT (float keys): the
+// lanes hold their values with alternating signs (odd lanes negated), so a
+// neighbour's edge value is negated before the comparison.
+template <int E, int L, bool ALT = false, typename T, typename KeyEq>
 __device__ __forceinline__ int seg_first_run_start(const T (&v)[E], int ls, KeyEq eq,
                                                    bool& cont_right) {
   const int pos0 = E * ls;
   T prev = __shfl_up_sync(FULL_MASK, v[E - 1], 1, L);
   T next = __shfl_down_sync(FULL_MASK, v[0], 1, L);
+  if constexpr (ALT) {
+    prev = -prev;
+    next = -next;
+  }
   const bool cont_left = (ls > 0) && eq(prev, v[0]);
   cont_right = (ls < L - 1) && eq(v[E - 1], next);
   int cnt_last = 0;

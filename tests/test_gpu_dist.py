@@ -199,3 +199,56 @@ def test_delta_rows_differing_by_a_constant_vector_are_zero(G, p, nus):
     Y0 = torch.from_numpy(wl.y_init(n, 2, seed=901)).cuda()
     with pytest.raises(GiniError, match="EDEGENERATE"):
         G.gini_mds_fit(Y0, nus[0], D, 1.0, 3, history=False)
+
+
+@pytest.mark.parametrize("nus", [[1.3], [1.3, 2.0, 3.7, 5.0]])
+def test_delta_exact_order_within_one_fp32_cell(G, nus):
+    # Three differences strictly between 1 and the next float up, two of them
+    # equal: 1 + 2^-26 (twice) and 1 + 2^-25.  Their cell keys tie; the exact
+    # order (and the tie of the equal two) must still give the oracle's ranks.
+    rng = np.random.default_rng(5100)
+    n, p = 20, 47
+    X = rng.uniform(-0.5, 0.5, (n, p)).astype(np.float32)
+    X[0, :3] = [1.0, 1.0, 1.0]
+    X[1, :3] = [-2.0 ** -26, -2.0 ** -25, -2.0 ** -26]
+    z = X[0].astype(np.float32) - X[1].astype(np.float32)
+    assert z[0] == z[1] == z[2] == 1.0  # all three round to 1.0f
+    D, sd2 = orc.delta(X, nus)
+    for layout in ("full", "tiled"):
+        mats, s2 = G.gini_dist(torch.from_numpy(X).cuda(), nus, layout=layout, dtype="f32")
+        for v in range(len(nus)):
+            got = mats[v].data.cpu().numpy().astype(np.float64)
+            if layout == "tiled":
+                got = untile(got, n)
+                got = got + got.T
+            assert abs(got[0, 1] - D[v][0, 1]) <= 2e-6 * abs(D[v][0, 1]), (nus[v], layout)
+            assert np.max(np.abs(got - D[v])) <= 1e-5 * np.abs(D[v]).max()
+            assert s2[v].item() == pytest.approx(sd2[v], rel=1e-6)
+
+
+@pytest.mark.parametrize("p", [6, 100, 784])
+def test_delta_wide_range_data_take_the_64bit_network(G, p):
+    # A range of 1e4 with nonzero values near 1e-38: scaling the cell keys by
+    # 2^-14 would push those below the normal range, so the pre-pass sends the
+    # build to the 64-bit TwoSum network.  Results must match the oracle.
+    rng = np.random.default_rng(5200 + p)
+    n = 33
+    X = (rng.standard_normal((n, p)) * 3000).astype(np.float32)
+    X[rng.integers(0, n, 8), rng.integers(0, p, 8)] = np.float32(3e-38)
+    nus = [1.7, 2.5]
+    D, sd2 = orc.delta(X, nus)
+    mats, s2 = G.gini_dist(torch.from_numpy(X).cuda(), nus, layout="full")
+    for v in range(2):
+        got = mats[v].data.cpu().numpy().astype(np.float64)
+        _check_full(got, D[v])
+        assert s2[v].item() == pytest.approx(sd2[v], rel=1e-5)
+
+
+def test_delta_sum_of_squares_is_run_to_run_identical(G):
+    # Sum delta^2 is accumulated exactly (128-bit integer units), so repeated
+    # builds return the same bits whatever order the CTAs finish in.
+    X = torch.from_numpy(wl.make_X("image-n2000-p784")[:1500]).cuda()
+    for nus in ([2.0], [1.5, 3.0]):
+        a = [G.gini_dist(X, nus, layout="tiled", dtype="f32")[1].cpu().numpy() for _ in range(3)]
+        for b in a[1:]:
+            np.testing.assert_array_equal(a[0], b)
