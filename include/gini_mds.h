@@ -94,7 +94,9 @@ typedef enum {
   GINI_OP_RANK = 0,
   GINI_OP_DIST = 1,
   GINI_OP_STRESS = 2,
-  GINI_OP_FIT = 3
+  GINI_OP_FIT = 3,
+  GINI_OP_STRESS_DET = 4,  /* GINI_OP_STRESS in deterministic mode (larger) */
+  GINI_OP_FIT_DET = 5      /* GINI_OP_FIT in deterministic mode (larger) */
 } gini_op;
 
 /* Human-readable name of a status code (static string). */
@@ -122,6 +124,27 @@ int64_t gini_tiled_elems(int64_t n);
  * embedding dimension; iters: iterations (FIT).  Unused arguments are ignored.
  * Returns 0 for an unknown op. */
 size_t gini_workspace_size(int op, int64_t n, int64_t m, int k, int iters);
+
+/* Deterministic mode for the calling host thread (0 at start; no
+ * counterpart in the paper).  Two things are reduced in a fixed order in
+ * every mode, whatever order the CTAs finish in:
+ *   - each pass's stress (every CTA stores a partial in its own slot, and the
+ *     slots are summed in index order);
+ *   - Sum delta^2 of gini_dist (an exact 128-bit integer accumulator).
+ * With the mode on, the tiled fused kernels also stop adding row and column
+ * gradient terms with float atomics.  They write per-tile partials, which one
+ * more kernel per pass sums point by point in a fixed order.  The results of
+ * gini_stress_grad(_ex), gini_mds_fit, gini_fit_batched and gini_nu_search
+ * are then bit-identical from run to run for equal inputs on one device and
+ * library build, and a fit resumed from its own Y_t continues bit for bit.
+ * Cost: a few percent per iteration, and the larger workspaces of
+ * GINI_OP_STRESS_DET / GINI_OP_FIT_DET (2 B k floats per stored tile, about n^2 k / 32
+ * bytes, B = gini_tile_size()).  The plain (FULL) form is deterministic in both
+ * modes. */
+void gini_set_deterministic(int on);
+
+/* The calling thread's deterministic mode (0 or 1). */
+int gini_get_deterministic(void);
 
 /* Synchronizes `stream`, then returns and clears the status the kernels
  * recorded in `ws` since the last gini_check (GINI_OK, GINI_ENONFINITE or
@@ -257,6 +280,8 @@ typedef struct {
   int metric;                 /* gini_metric (0: Gini) */
   int loss;                   /* gini_loss (0: Kruskal); sum_delta2 then holds the loss's
                                  normaliser (sum delta^2, or sum delta for Sammon) */
+  int deterministic;          /* 1: fixed-order gradient reductions (see
+                                 gini_set_deterministic); 0: the thread's setting */
 } gini_fit_args;
 
 /* T iterations of Y_{t+1} = Y_t - eta * dS/dY(Y_t) (the "Run MDS" step of
@@ -275,7 +300,7 @@ typedef struct {
 
 /* Bytes of workspace gini_fit_batched needs for these problems. */
 size_t gini_batch_workspace_size(const gini_problem* probs, int nprob, int n_nu, int restarts,
-                                 int iters);
+                                 int iters, int deterministic);
 
 /* Many k = 2 fits at once: every problem x every nu of the grid x `restarts`
  * starting points (the loops of Algorithm 1 over nu and starts).  For each
@@ -298,11 +323,16 @@ size_t gini_batch_workspace_size(const gini_problem* probs, int nprob, int n_nu,
  *                fits are ordered (problem, nu, restart)
  *   final_stress_dev  nfits doubles out, S(Y_T)
  *   tuned_config out (host), or NULL: 100 x rows-per-warp + CTAs per SM chosen
+ *   deterministic  1: per (tile, restart) partials summed in a fixed order
+ *                instead of atomics, so results repeat bit for bit (also on when
+ *                the thread's mode is, gini_set_deterministic); it needs the
+ *                workspace gini_batch_workspace_size(..., 1) reports (about
+ *                1 KB more per tile and restart)
  * Non-finite data are reported by gini_check(ws, stream). */
 int gini_fit_batched(const gini_problem* probs, int nprob, const double* nu_host, int n_nu,
                      int restarts, int iters, double eta0, const float* Y0_dev, float* Y_dev,
-                     double* history_dev, double* final_stress_dev, int* tuned_config, void* ws,
-                     size_t ws_bytes, void* stream);
+                     double* history_dev, double* final_stress_dev, int* tuned_config,
+                     int deterministic, void* ws, size_t ws_bytes, void* stream);
 
 /* Bytes of workspace gini_nu_search needs (0 on invalid folds or sizes). */
 size_t gini_nu_search_workspace_size(int64_t n, int64_t p, const int32_t* fold_host, int K,

@@ -16,7 +16,7 @@ DTYPES = {"f32": 0, "bf16": 1, "bf16x2": 2, "fp8": 3}
 METRICS = {"gini": 0, "euclid": 1}
 LOSSES = {"kruskal": 0, "sammon": 1}
 LAYOUTS = {"full": 0, "tiled": 1}
-OPS = {"rank": 0, "dist": 1, "stress": 2, "fit": 3}
+OPS = {"rank": 0, "dist": 1, "stress": 2, "fit": 3, "stress_det": 4, "fit_det": 5}
 
 _c = ctypes
 _vp = _c.c_void_p
@@ -36,7 +36,7 @@ class FitArgs(_c.Structure):
         ("col_scale_dev", _vp), ("sum_delta2", _c.c_double), ("eta", _c.c_double),
         ("iters", _c.c_int), ("polish_iters", _c.c_int), ("Y_dev", _vp),
         ("history_dev", _vp), ("final_stress_dev", _vp), ("metric", _c.c_int),
-        ("loss", _c.c_int),
+        ("loss", _c.c_int), ("deterministic", _c.c_int),
     ]
 
 
@@ -86,10 +86,12 @@ SIGNATURES = {
                                             _c.c_int, _i64, _vp, _c.c_double, _vp, _vp, _vp]),
     "gini_default_step": (_c.c_double, [_i64, _c.c_int, _c.c_double, _c.c_double, _c.c_double]),
     "gini_batch_workspace_size": (_c.c_size_t, [_c.POINTER(Problem), _c.c_int, _c.c_int,
-                                                _c.c_int, _c.c_int]),
+                                                _c.c_int, _c.c_int, _c.c_int]),
     "gini_fit_batched": (_c.c_int, [_c.POINTER(Problem), _c.c_int, _c.POINTER(_c.c_double),
                                     _c.c_int, _c.c_int, _c.c_int, _c.c_double, _vp, _vp, _vp,
-                                    _vp, _c.POINTER(_c.c_int), _vp, _c.c_size_t, _vp]),
+                                    _vp, _c.POINTER(_c.c_int), _c.c_int, _vp, _c.c_size_t, _vp]),
+    "gini_set_deterministic": (None, [_c.c_int]),
+    "gini_get_deterministic": (_c.c_int, []),
 }
 
 _lib = None

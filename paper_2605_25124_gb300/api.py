@@ -71,6 +71,35 @@ def workspace_size(op: str, n: int, m: int = 0, k: int = 0, iters: int = 0) -> i
     return int(lib().gini_workspace_size(OPS[op], int(n), int(m), int(k), int(iters)))
 
 
+class deterministic:
+    """Deterministic mode of the library for the calling thread
+    (gini_set_deterministic), as a context manager or a plain call:
+
+        with G.deterministic():        # fixed-order reductions inside
+            Y, hist, S = G.gini_mds_fit(...)
+        G.deterministic(True).apply()  # stays on
+    """
+
+    def __init__(self, on: bool = True):
+        self.on = bool(on)
+        self.prev = None
+
+    def apply(self):
+        lib().gini_set_deterministic(int(self.on))
+        return self
+
+    def __enter__(self):
+        self.prev = bool(lib().gini_get_deterministic())
+        return self.apply()
+
+    def __exit__(self, *exc):
+        lib().gini_set_deterministic(int(self.prev))
+
+
+def is_deterministic() -> bool:
+    return bool(lib().gini_get_deterministic())
+
+
 def default_step(n: int, k: int, nu: float, sum_delta2: float, eta0: float = 1.0) -> float:
     return float(lib().gini_default_step(int(n), int(k), float(nu), float(sum_delta2),
                                          float(eta0)))
@@ -176,7 +205,7 @@ def gini_stress_grad(Y: torch.Tensor, nu: float, D: Dissimilarity, grad: bool = 
     stress = torch.empty((), dtype=torch.float64, device=Y.device)
     g = torch.empty_like(Y) if grad else None
     ws = ws or workspace(Y.device)
-    buf = ws.ensure(workspace_size("stress", n, 0, k))
+    buf = ws.ensure(workspace_size("stress_det" if is_deterministic() else "stress", n, 0, k))
     nrm = D.sum_delta2 if norm is None else float(norm)
     st = lib().gini_stress_grad_ex(_ptr(Y), n, k, float(nu), _ptr(D.data), LAYOUTS[D.layout],
                                    DTYPES[D.dtype], D.ldd, _ptr(D.col_scale), METRICS[metric],
@@ -191,8 +220,11 @@ def gini_stress_grad(Y: torch.Tensor, nu: float, D: Dissimilarity, grad: bool = 
 def gini_mds_fit(Y0: torch.Tensor, nu: float, D: Dissimilarity, eta: float, iters: int,
                  polish_iters: int = 0, history: bool = True, ws: Optional[Workspace] = None,
                  check_errors: bool = True, out: Optional[torch.Tensor] = None,
-                 metric: str = "gini", loss: str = "kruskal", norm: Optional[float] = None):
-    """Fixed-step GD on the normalized stress; returns (Y_T, history or None, S(Y_T))."""
+                 metric: str = "gini", loss: str = "kruskal", norm: Optional[float] = None,
+                 deterministic: bool = False):
+    """Fixed-step GD on the normalized stress; returns (Y_T, history or None, S(Y_T)).
+    deterministic: fixed-order gradient reductions for this call (also on when
+    the thread's mode is)."""
     _require_cuda(Y0)
     n, k = Y0.shape
     Y = out if out is not None else Y0.clone()
@@ -201,8 +233,9 @@ def gini_mds_fit(Y0: torch.Tensor, nu: float, D: Dissimilarity, eta: float, iter
     hist = torch.empty(iters + 1, dtype=torch.float64, device=Y0.device) if history else None
     final = torch.empty((), dtype=torch.float64, device=Y0.device)
     ws = ws or workspace(Y0.device)
-    buf = ws.ensure(workspace_size("fit", n, 0, k, iters))
-    a = _lib.FitArgs(n=n, k=k, nu=float(nu), delta_dev=D.data.data_ptr(),
+    det = bool(deterministic) or is_deterministic()
+    buf = ws.ensure(workspace_size("fit_det" if det else "fit", n, 0, k, iters))
+    a = _lib.FitArgs(deterministic=int(det), n=n, k=k, nu=float(nu), delta_dev=D.data.data_ptr(),
                      layout=LAYOUTS[D.layout], dtype=DTYPES[D.dtype], ldd=D.ldd,
                      col_scale_dev=(D.col_scale.data_ptr() if D.col_scale is not None else None),
                      sum_delta2=(D.sum_delta2 if norm is None else float(norm)),
@@ -220,7 +253,7 @@ def gini_mds_fit(Y0: torch.Tensor, nu: float, D: Dissimilarity, eta: float, iter
 
 def gini_fit_batched(Xs, nus, restarts: int, iters: int, Y0: torch.Tensor, eta0: float = 1.0,
                      history: bool = False, ws: Optional[Workspace] = None,
-                     check_errors: bool = True):
+                     check_errors: bool = True, deterministic: bool = False):
     """Batched k = 2 fits of every problem x nu x restart.
 
     Xs: list of (n_q, p_q) float32 CUDA tensors.  Y0: flat float32 tensor,
@@ -245,14 +278,15 @@ def gini_fit_batched(Xs, nus, restarts: int, iters: int, Y0: torch.Tensor, eta0:
     nfits = nprob * n_nu * restarts
     final = torch.empty(nfits, dtype=torch.float64, device=dev)
     hist = torch.empty((iters + 1) * nfits, dtype=torch.float64, device=dev) if history else None
-    nbytes = int(lib().gini_batch_workspace_size(probs, nprob, n_nu, restarts, iters))
+    det = int(bool(deterministic) or is_deterministic())
+    nbytes = int(lib().gini_batch_workspace_size(probs, nprob, n_nu, restarts, iters, det))
     ws = ws or workspace(dev)
     buf = ws.ensure(nbytes)
     nu_arr = (ctypes.c_double * n_nu)(*nus)
     tuned = ctypes.c_int(0)
     st = lib().gini_fit_batched(probs, nprob, nu_arr, n_nu, restarts, iters, float(eta0),
                                 _ptr(Y0.contiguous()), _ptr(Y), _ptr(hist), _ptr(final),
-                                ctypes.byref(tuned), _ptr(buf), buf.numel(), _stream())
+                                ctypes.byref(tuned), det, _ptr(buf), buf.numel(), _stream())
     check(st, "gini_fit_batched")
     if check_errors:
         ws.check()

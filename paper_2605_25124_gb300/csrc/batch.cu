@@ -53,6 +53,12 @@ struct BatchParams {
   float* h;            // gradient accumulators
   double* acc;         // stress accumulators of the current pass: one per fit
   unsigned* err;
+  // Deterministic mode (else null): per (tile, restart) partials instead of
+  // atomics.  Work item g, restart r: row sums at part[((g R + r) 2) 128 ..],
+  // column sums at part[((g R + r) 2 + 1) 128 ..], stress at spart[g R + r];
+  // k_batch_det_reduce adds them up per point and per fit in a fixed order.
+  float* part;
+  float* spart;
 };
 
 __device__ __forceinline__ int find_seg(const BatchSeg* segs, int nseg, int64_t g) {
@@ -216,8 +222,10 @@ __global__ void __launch_bounds__(TILE / ROWS * 32) k_batch_iter(const BatchPara
       if (GRAD) {
         const float rs = reduce_rows<ROWS>(rowv, lane);
         if (lane < ROWS) {
-          const int64_t gi = i0 + warp * ROWS + row_of_lane<ROWS>(lane);
-          if (gi < n) atomicAdd(B.h + sg.h_off + r * n + gi, rs);
+          const int rl = warp * ROWS + row_of_lane<ROWS>(lane);
+          const int64_t gi = i0 + rl;
+          if (B.part) B.part[((g * R + r) * 2) * TILE + rl] = rs;
+          else if (gi < n) atomicAdd(B.h + sg.h_off + r * n + gi, rs);
         }
 #pragma unroll
         for (int c = 0; c < 4; ++c) s_col[buf][warp][4 * lane + c] = col[c];
@@ -228,15 +236,56 @@ __global__ void __launch_bounds__(TILE / ROWS * 32) k_batch_iter(const BatchPara
 #pragma unroll
         for (int w = 0; w < WARPS; ++w) v += s_col[buf][w][threadIdx.x];
         const int64_t gj = j0 + threadIdx.x;
-        if (gj < n) atomicAdd(B.h + sg.h_off + r * n + gj, v);
+        if (B.part) B.part[((g * R + r) * 2 + 1) * TILE + threadIdx.x] = v;
+        else if (gj < n) atomicAdd(B.h + sg.h_off + r * n + gj, v);
       }
       if (threadIdx.x == 0) {
         float v = 0.f;
         for (int w = 0; w < WARPS; ++w) v += s_S[buf][w];
-        atomicAdd(B.acc + sg.fit0 + r, (double)v);
+        if (B.spart) B.spart[g * R + r] = v;
+        else atomicAdd(B.acc + sg.fit0 + r, (double)v);
       }
       if constexpr (NBUF == 1) __syncthreads();
     }
+  }
+}
+
+// Deterministic mode: h of every (segment, restart, point) from the per-tile
+// partials, row tiles (I, J >= I) then column tiles (J' <= I, I) in order, and
+// (point 0's thread) the fit's stress from its tiles' partials in order.
+// One thread per (segment, restart, point), as k_batch_update.
+__global__ void k_batch_det_reduce(const BatchSeg* segs, int nseg, int R, const int64_t* pt_prefix,
+                                   int64_t total, const float* part, const float* spart,
+                                   float* h, double* acc) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= total) return;
+  int lo = 0, hi = nseg - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (pt_prefix[mid] <= e) lo = mid;
+    else hi = mid - 1;
+  }
+  const BatchSeg& sg = segs[lo];
+  const int64_t local = e - pt_prefix[lo];
+  const int r = (int)(local / sg.n);
+  const int64_t i = local % sg.n;
+  const int64_t I = i / TILE, T = sg.tiles;
+  const int rl = (int)(i % TILE);
+  float v = 0.f;
+  for (int64_t J = I; J < T; ++J) {
+    const int64_t g = sg.tile_begin + tile_offset(I, J, T);
+    v += part[((g * R + r) * 2) * TILE + rl];
+  }
+  for (int64_t J = 0; J <= I; ++J) {
+    const int64_t g = sg.tile_begin + tile_offset(J, I, T);
+    v += part[((g * R + r) * 2 + 1) * TILE + rl];
+  }
+  h[sg.h_off + (int64_t)r * sg.n + i] = v;
+  if (i == 0) {
+    double S = 0.0;
+    const int64_t nt = T * (T + 1) / 2;
+    for (int64_t t = 0; t < nt; ++t) S += (double)spart[(sg.tile_begin + t) * R + r];
+    acc[sg.fit0 + r] = S;
   }
 }
 
@@ -333,10 +382,13 @@ struct BatchWs {
   float* h;
   double* acc;
   float* wtab;
+  float* part;   // deterministic mode only
+  float* spart;
   size_t total;
 };
 
-static BatchWs batch_layout(const BatchPlan& pl, int nprob, int n_nu, int iters, char* base) {
+static BatchWs batch_layout(const BatchPlan& pl, int nprob, int n_nu, int iters, bool det,
+                            char* base) {
   BatchWs w{};
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -356,6 +408,9 @@ static BatchWs batch_layout(const BatchPlan& pl, int nprob, int n_nu, int iters,
   w.P = (float2*)take(sizeof(float2) * (size_t)pl.pts);
   w.h = (float*)take(sizeof(float) * (size_t)pl.hs);
   w.acc = (double*)take(sizeof(double) * (size_t)(iters + 1) * pl.nfits);
+  const size_t items = (size_t)pl.total_tiles * (pl.nfits / std::max<size_t>(1, pl.segs.size()));
+  w.part = det ? (float*)take(sizeof(float) * items * 2 * TILE) : nullptr;
+  w.spart = det ? (float*)take(sizeof(float) * items) : nullptr;
   w.total = off;
   return w;
 }
@@ -491,20 +546,21 @@ static GraphEntry g_graph;
 using namespace gini;
 
 extern "C" void gini_set_cuda_error(cudaError_t e);
+extern "C" int gini_get_deterministic(void);
 
 extern "C" size_t gini_batch_workspace_size(const gini_problem* probs, int nprob, int n_nu,
-                                            int restarts, int iters) {
+                                            int restarts, int iters, int deterministic) {
   if (!probs || nprob < 1 || n_nu < 1 || restarts < 1 || iters < 0) return 0;
   std::vector<double> nu(n_nu, 2.0);
   BatchPlan pl = make_plan(probs, nprob, nu.data(), n_nu, restarts, 1.0);
-  return batch_layout(pl, nprob, n_nu, iters, nullptr).total;
+  return batch_layout(pl, nprob, n_nu, iters, deterministic != 0, nullptr).total;
 }
 
 extern "C" int gini_fit_batched(const gini_problem* probs, int nprob, const double* nu_host,
                                 int n_nu, int restarts, int iters, double eta0,
                                 const float* Y0_dev, float* Y_dev, double* history_dev,
-                                double* final_stress_dev, int* tuned_rows, void* ws,
-                                size_t ws_bytes, void* stream) {
+                                double* final_stress_dev, int* tuned_rows, int deterministic,
+                                void* ws, size_t ws_bytes, void* stream) {
   if (!probs || !nu_host || !Y0_dev || !Y_dev || !ws) return GINI_EINVAL;
   if (ws_misaligned(ws)) return GINI_EINVAL;
   if (nprob < 1 || n_nu < 1 || n_nu > 8 || restarts < 1 || restarts > BATCH_RMAX || iters < 0)
@@ -519,7 +575,8 @@ extern "C" int gini_fit_batched(const gini_problem* probs, int nprob, const doub
   }
   BatchPlan pl = make_plan(probs, nprob, nu_host, n_nu, restarts, eta0);
   if (pl.nfits > (1 << 30)) return GINI_EINVAL;
-  BatchWs w = batch_layout(pl, nprob, n_nu, iters, reinterpret_cast<char*>(ws));
+  const bool det = deterministic || gini_get_deterministic();
+  BatchWs w = batch_layout(pl, nprob, n_nu, iters, det, reinterpret_cast<char*>(ws));
   if (ws_bytes < w.total) return GINI_ENOMEM;
   cudaStream_t s = (cudaStream_t)stream;
 
@@ -555,7 +612,15 @@ extern "C" int gini_fit_batched(const gini_problem* probs, int nprob, const doub
   P.P = w.P;
   P.h = w.h;
   P.err = w.err;
+  P.part = w.part;
+  P.spart = w.spart;
   const int nseg = (int)pl.segs.size();
+  // deterministic mode: h and each fit's stress from the partials of a pass
+  auto det_reduce = [&](double* acc) {
+    gini_count_launch(1);
+    k_batch_det_reduce<<<(unsigned)((pl.total_upd + 255) / 256), 256, 0, s>>>(
+        w.segs, nseg, restarts, w.pt_prefix, pl.total_upd, w.part, w.spart, w.h, acc);
+  };
   auto init = [&]() {
     gini_count_launch(1);
     k_batch_init<<<(unsigned)((pl.total_pad + 255) / 256), 256, 0, s>>>(
@@ -570,9 +635,9 @@ extern "C" int gini_fit_batched(const gini_problem* probs, int nprob, const doub
 
   // 4. The fit as one graph: reset, T x (iteration + update), final pass, finalize.
   char keybuf[512];
-  snprintf(keybuf, sizeof(keybuf), "%p/%p/%p/%p/%p/%d/%d/%d/%lld/%d/%d", ws, (const void*)Y0_dev,
-           (void*)Y_dev, (void*)history_dev, (void*)final_stress_dev, iters, restarts, nprob,
-           (long long)pl.total_tiles, tc.rows, tc.per_sm);
+  snprintf(keybuf, sizeof(keybuf), "%p/%p/%p/%p/%p/%d/%d/%d/%lld/%d/%d/%d", ws,
+           (const void*)Y0_dev, (void*)Y_dev, (void*)history_dev, (void*)final_stress_dev, iters,
+           restarts, nprob, (long long)pl.total_tiles, tc.rows, tc.per_sm, det ? 1 : 0);
   std::string key(keybuf);
   for (int q = 0; q < nprob; ++q) key += "/" + std::to_string((long long)probs[q].n);
   for (int v = 0; v < n_nu; ++v) key += "/" + std::to_string(nu_host[v]);
@@ -597,12 +662,14 @@ extern "C" int gini_fit_batched(const gini_problem* probs, int nprob, const doub
       for (int t = 0; t < iters; ++t) {
         P.acc = w.acc + (size_t)t * pl.nfits;
         launch_iter(tc, true, P, s);
+        if (det) det_reduce(P.acc);
         gini_count_launch(1);
         k_batch_update<<<(unsigned)((pl.total_upd + 255) / 256), 256, 0, s>>>(
             w.segs, nseg, restarts, w.pt_prefix, pl.total_upd, Y_dev, w.P, w.h, w.err);
       }
       P.acc = w.acc + (size_t)iters * pl.nfits;
       launch_iter(tc, false, P, s);
+      if (det) det_reduce(P.acc);
       const int64_t nfin = (int64_t)(iters + 1) * pl.nfits;
       gini_count_launch(1);
       k_batch_finalize<<<(unsigned)((nfin + 255) / 256), 256, 0, s>>>(

@@ -15,7 +15,7 @@ extern "C" void gini_count_launch(unsigned n) { g_launches.fetch_add(n, std::mem
 
 extern "C" uint64_t gini_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
-extern "C" size_t gini_iter_ws_bytes(int64_t n, int k, int nacc);
+extern "C" size_t gini_iter_ws_bytes(int64_t n, int k, int nacc, int det);
 
 extern "C" void gini_set_cuda_error(cudaError_t e) {
   strncpy(g_cuda_err, cudaGetErrorString(e), sizeof(g_cuda_err) - 1);
@@ -37,7 +37,14 @@ extern "C" const char* gini_status_str(int status) {
   }
 }
 
-extern "C" int gini_version(void) { return 1; }
+extern "C" int gini_version(void) { return 2; }
+
+// Deterministic mode of the calling host thread (see gini_set_deterministic).
+static thread_local int g_deterministic = 0;
+
+extern "C" void gini_set_deterministic(int on) { g_deterministic = on ? 1 : 0; }
+
+extern "C" int gini_get_deterministic(void) { return g_deterministic; }
 
 extern "C" int gini_tile_size(void) { return TILE; }
 
@@ -53,8 +60,11 @@ extern "C" size_t gini_workspace_size(int op, int64_t n, int64_t m, int k, int i
       const int64_t mm = m < 1 ? 1 : m;
       return WS_HEADER + 256 + (size_t)8 * (size_t)(2 * mm - 1) * sizeof(float);
     }
-    case GINI_OP_STRESS: return gini_iter_ws_bytes(n, k < 2 ? 2 : k, 1);
-    case GINI_OP_FIT: return gini_iter_ws_bytes(n, k < 2 ? 2 : k, (iters < 0 ? 0 : iters) + 1);
+    case GINI_OP_STRESS: return gini_iter_ws_bytes(n, k < 2 ? 2 : k, 1, 0);
+    case GINI_OP_FIT: return gini_iter_ws_bytes(n, k < 2 ? 2 : k, (iters < 0 ? 0 : iters) + 1, 0);
+    case GINI_OP_STRESS_DET: return gini_iter_ws_bytes(n, k < 2 ? 2 : k, 1, 1);
+    case GINI_OP_FIT_DET:
+      return gini_iter_ws_bytes(n, k < 2 ? 2 : k, (iters < 0 ? 0 : iters) + 1, 1);
     default: return 0;
   }
 }

@@ -22,6 +22,8 @@
 //          its column's gradient (d_ji = d_ij, antisymmetric derivative).
 #include <math.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "pipe.cuh"
 
@@ -29,6 +31,10 @@ namespace gini {
 
 constexpr int KMAX = 8;
 constexpr int FUSED_THREADS = 256;  // 8 warps; a warp owns 16 rows of a 128 x 128 tile
+// Stress of one pass: every CTA stores its FP64 partial in its own slot, and
+// the slots are summed in index order afterwards, so the stress does not
+// depend on the order the CTAs finish in.  Grids are capped at this count.
+constexpr int STRESS_SLOTS = 1024;
 
 struct PairTab {
   float c2;               // k = 2: 2^{1-nu}
@@ -45,7 +51,12 @@ struct IterParams {
   int64_t tiles;
   int64_t plane;
   float* h;          // k = 2: n scalars sum_j r_ij sign; else n x k sums of r_ij T
-  double* stress;    // FP64 accumulator of sum r^2
+  double* stress;    // STRESS_SLOTS FP64 slots of this pass (slot = CTA index)
+  // Deterministic mode (else null): per-tile gradient partials instead of
+  // atomics into h.  Tile t's row sums at part[(2t) 128 kp ..], its column sums
+  // at part[(2t+1) 128 kp ..], kp = 1 on the scalar k = 2 path, else k
+  // components per point; k_det_reduce sums them per point in a fixed order.
+  float* part;
   PairTab tab;
   unsigned* err;
   int metric;        // GINI_METRIC_GINI or GINI_METRIC_EUCLID
@@ -285,7 +296,7 @@ __global__ void __launch_bounds__(256) k_full(const IterParams Q) {
     if (threadIdx.x == 0) {
       double s = 0.0;
       for (int w = 0; w < 8; ++w) s += s_red[w];
-      atomicAdd(Q.stress, s);
+      Q.stress[blockIdx.x] = s;
     }
   }
 }
@@ -325,7 +336,8 @@ __device__ __forceinline__ void load4(const IterParams& Q, int64_t off, float (&
   }
 }
 
-__device__ __forceinline__ void block_add_stress(double v, double* dst) {
+// Sums v over the CTA in a fixed order and stores it in the CTA's stress slot.
+__device__ __forceinline__ void block_store_stress(double v, double* slots) {
   __shared__ double s_red[FUSED_THREADS / 32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
@@ -335,7 +347,7 @@ __device__ __forceinline__ void block_add_stress(double v, double* dst) {
   if (threadIdx.x == 0) {
     double s = 0.0;
     for (int w = 0; w < FUSED_THREADS / 32; ++w) s += s_red[w];
-    atomicAdd(dst, s);
+    slots[blockIdx.x] = s;
   }
 }
 
@@ -566,7 +578,7 @@ __global__ void __launch_bounds__(PIPE_THREADS) k_fused2(const IterParams Q, int
     if (h == 0) {
       if (c > 0) tile_next(I, J, Q.tiles);
       if (GRAD && I != curI) {
-        if (curI >= 0 && lane < 8) {
+        if (!Q.part && curI >= 0 && lane < 8) {
           const int64_t gi = (int64_t)curI * TILE + warp * 8 + rev3(lane);
           if (gi < n) atomicAdd(Q.h + gi, rowacc0);
           if (gi + CHUNK_ROWS < n) atomicAdd(Q.h + gi + CHUNK_ROWS, rowacc1);
@@ -624,6 +636,13 @@ __global__ void __launch_bounds__(PIPE_THREADS) k_fused2(const IterParams Q, int
       if (h) rowacc1 += rs;
       else rowacc0 += rs;
       if (h == 1) {
+        const int64_t tcur = t_begin + (c >> 1);
+        if (Q.part && lane < 8) {  // deterministic: this tile's row sums
+          float* rp = Q.part + (2 * tcur) * TILE + warp * 8 + rev3(lane);
+          rp[0] = rowacc0;
+          rp[CHUNK_ROWS] = rowacc1;
+          rowacc0 = rowacc1 = 0.f;
+        }
         float* cw = s_colw[(c >> 1) & 1][warp];
         *reinterpret_cast<float4*>(cw + 4 * lane) =
             make_float4(col2[0].x, col2[0].y, col2[1].x, col2[1].y);
@@ -633,12 +652,13 @@ __global__ void __launch_bounds__(PIPE_THREADS) k_fused2(const IterParams Q, int
 #pragma unroll
           for (int w = 0; w < CONSUMER_WARPS; ++w) v += s_colw[(c >> 1) & 1][w][threadIdx.x];
           const int64_t gj = (int64_t)J * TILE + threadIdx.x;
-          if (gj < n) atomicAdd(Q.h + gj, v);
+          if (Q.part) Q.part[(2 * tcur + 1) * TILE + threadIdx.x] = v;
+          else if (gj < n) atomicAdd(Q.h + gj, v);
         }
       }
     }
   }
-  if (GRAD && curI >= 0 && lane < 8) {
+  if (GRAD && !Q.part && curI >= 0 && lane < 8) {
     const int64_t gi = (int64_t)curI * TILE + warp * 8 + rev3(lane);
     if (gi < n) atomicAdd(Q.h + gi, rowacc0);
     if (gi + CHUNK_ROWS < n) atomicAdd(Q.h + gi + CHUNK_ROWS, rowacc1);
@@ -651,7 +671,7 @@ __global__ void __launch_bounds__(PIPE_THREADS) k_fused2(const IterParams Q, int
   if (threadIdx.x == 0) {
     double v = 0.0;
     for (int w = 0; w < CONSUMER_WARPS; ++w) v += s_red[w];
-    atomicAdd(Q.stress, v);
+    Q.stress[blockIdx.x] = v;
   }
 }
 
@@ -672,6 +692,8 @@ __global__ void __launch_bounds__(FUSED_THREADS) k_fusedk(const IterParams Q, in
   constexpr int NP = K * (K - 1) / 2;
   extern __shared__ __align__(16) unsigned char s_raw[];
   FusedKSmem<K>& sm = *reinterpret_cast<FusedKSmem<K>*>(s_raw);
+  // deterministic mode: per-warp column sums (8 x 128 x K floats after sm)
+  float* det_cols = reinterpret_cast<float*>(s_raw + sizeof(FusedKSmem<K>));
   auto& s_p = sm.p;
   auto& s_y = sm.y;
   auto& s_colh = sm.colh;
@@ -864,8 +886,12 @@ __global__ void __launch_bounds__(FUSED_THREADS) k_fusedk(const IterParams Q, in
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
               const float v = reduce8(racc8[a], lane);
-              const int64_t gi = i0 + warp * 16 + rb + rev3(lane & 7);
-              if (lane < 8 && gi < Q.n) atomicAdd(Q.h + gi * K + a, v);
+              const int rl = warp * 16 + rb + rev3(lane & 7);
+              const int64_t gi = i0 + rl;
+              if (lane < 8) {
+                if (Q.part) Q.part[(2 * t * TILE + rl) * K + a] = v;
+                else if (gi < Q.n) atomicAdd(Q.h + gi * K + a, v);
+              }
             }
           }
         }
@@ -907,8 +933,12 @@ __global__ void __launch_bounds__(FUSED_THREADS) k_fusedk(const IterParams Q, in
 #pragma unroll
           for (int a = 0; a < K; ++a) {
             const float v = reduce8(racc8[a], lane);
-            const int64_t gi = i0 + warp * 16 + rb + rev3(lane & 7);
-            if (lane < 8 && gi < Q.n) atomicAdd(Q.h + gi * K + a, v);
+            const int rl = warp * 16 + rb + rev3(lane & 7);
+            const int64_t gi = i0 + rl;
+            if (lane < 8) {
+              if (Q.part) Q.part[(2 * t * TILE + rl) * K + a] = v;
+              else if (gi < Q.n) atomicAdd(Q.h + gi * K + a, v);
+            }
           }
         }
       }
@@ -929,14 +959,32 @@ __global__ void __launch_bounds__(FUSED_THREADS) k_fusedk(const IterParams Q, in
 #pragma unroll
             for (int o = 16; o >= 1; o >>= 1) racc[a] += __shfl_xor_sync(FULL_MASK, racc[a], o);
           }
-          if (lane == 0 && gi < Q.n)
+          if (lane == 0 && Q.part) {
+#pragma unroll
+            for (int a = 0; a < K; ++a) Q.part[(2 * t * TILE + rl) * K + a] = racc[a];
+          } else if (lane == 0 && gi < Q.n) {
 #pragma unroll
             for (int a = 0; a < K; ++a) atomicAdd(Q.h + gi * K + a, racc[a]);
+          }
         }
       }
     }
     Sd += (double)S;
-    if (GRAD) {
+    if (GRAD && Q.part) {
+      // deterministic: every warp's column sums in its own slice, summed over
+      // the warps in order
+      float* cw = det_cols + warp * TILE * K;
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int a = 0; a < K; ++a) cw[(4 * lane + c) * K + a] = colacc[c][a];
+      __syncthreads();
+      for (int e = threadIdx.x; e < TILE * K; e += FUSED_THREADS) {
+        float v = 0.f;
+        for (int w = 0; w < FUSED_THREADS / 32; ++w) v += det_cols[w * TILE * K + e];
+        Q.part[(2 * t + 1) * TILE * K + e] = v;
+      }
+    } else if (GRAD) {
 #pragma unroll
       for (int c = 0; c < 4; ++c)
 #pragma unroll
@@ -951,7 +999,7 @@ __global__ void __launch_bounds__(FUSED_THREADS) k_fusedk(const IterParams Q, in
       }
     }
   }
-  block_add_stress(Sd, Q.stress);
+  block_store_stress(Sd, Q.stress);
 }
 
 // ------------------------------------------------------ update, finalize ---
@@ -1008,12 +1056,53 @@ __global__ void k_finalize_grad(const float* __restrict__ h, int64_t n, int k, f
   }
 }
 
-__global__ void k_finalize_stress(const double* acc, int cnt, double inv_sd2, double* hist,
+// S of each of cnt passes: one warp per pass sums its STRESS_SLOTS slots in a
+// fixed order (lane-strided, then a shuffle tree), times 1 / normaliser.
+__global__ void k_finalize_stress(const double* slots, int cnt, double inv_sd2, double* hist,
                                   double* final_out) {
-  for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
-    const double v = acc[t] * inv_sd2;
+  const int t = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (t >= cnt) return;
+  const double* sl = slots + (size_t)t * STRESS_SLOTS;
+  double v = 0.0;
+  for (int k = lane; k < STRESS_SLOTS; k += 32) v += sl[k];
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(FULL_MASK, v, o);
+  if (lane == 0) {
+    v *= inv_sd2;
     if (hist) hist[t] = v;
     if (final_out && t == cnt - 1) final_out[0] = v;
+  }
+}
+
+// Deterministic mode: the gradient accumulators h from the per-tile partials
+// (IterParams::part), every point's terms added in the same order on every
+// run.  CTA = one tile row I (128 points) x 8 groups; group g takes the tiles
+// (I, J) with J = I + g, I + g + 8, ... (row sums) and (J', I) with J' = g,
+// g + 8, ... <= I (column sums); the 8 group sums are added in group order.
+__global__ void __launch_bounds__(8 * TILE) k_det_reduce(const float* __restrict__ part,
+                                                       int64_t n, int64_t T, int kp,
+                                                       float* __restrict__ h) {
+  __shared__ float s_g[8][TILE * KMAX];
+  const int64_t I = blockIdx.x;
+  const int g = threadIdx.x / TILE, r = threadIdx.x % TILE;
+  for (int a = 0; a < kp; ++a) {
+    float v = 0.f;
+    for (int64_t J = I + g; J < T; J += 8)
+      v += part[(2 * tile_offset(I, J, T) * TILE + r) * kp + a];
+    for (int64_t J = g; J <= I; J += 8)
+      v += part[((2 * tile_offset(J, I, T) + 1) * TILE + r) * kp + a];
+    s_g[g][r * kp + a] = v;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < TILE * kp; e += blockDim.x) {
+    const int64_t i = I * TILE + e / kp;
+    if (i < n) {
+      float v = 0.f;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) v += s_g[q][e];
+      h[i * kp + e % kp] = v;
+    }
   }
 }
 
@@ -1022,7 +1111,8 @@ __global__ void k_finalize_stress(const double* acc, int cnt, double inv_sd2, do
 struct IterWs {
   float2* P;
   float* h;
-  double* acc;
+  double* acc;   // nacc x STRESS_SLOTS stress slots
+  float* part;   // deterministic mode: per-tile gradient partials, else null
   unsigned* err;
 };
 
@@ -1033,29 +1123,39 @@ static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 using namespace gini;
 
 extern "C" void gini_set_cuda_error(cudaError_t e);
+extern "C" int gini_get_deterministic(void);
 
-// Workspace of the iteration ops: header | nacc doubles | point pairs | h.
-// Point pairs are stored for ceil(n / B) * B points (whole tiles, the padding
-// zero-filled) so that bulk copies of a tile's points never leave the array.
+// Workspace of the iteration ops: header | nacc x STRESS_SLOTS doubles | point
+// pairs | h | (deterministic mode) per-tile gradient partials.  Point pairs are
+// stored for ceil(n / B) * B points (whole tiles, the padding zero-filled) so
+// that bulk copies of a tile's points never leave the array.
 static int64_t padded_points(int64_t n) { return tiles_1d(n) * TILE; }
 
-extern "C" size_t gini_iter_ws_bytes(int64_t n, int k, int nacc) {
-  const int np = k * (k - 1) / 2;
-  return WS_HEADER + align256(sizeof(double) * (size_t)nacc) +
-         align256(sizeof(float2) * (size_t)padded_points(n) * np) +
-         align256(sizeof(float) * (size_t)n * k);
+static size_t part_floats(int64_t n, int k) {
+  const int64_t T = tiles_1d(n);
+  return (size_t)(T * (T + 1) / 2) * 2 * TILE * (size_t)k;
 }
 
-static IterWs carve(void* ws, int64_t n, int k, int nacc) {
+extern "C" size_t gini_iter_ws_bytes(int64_t n, int k, int nacc, int det) {
+  const int np = k * (k - 1) / 2;
+  return WS_HEADER + align256(sizeof(double) * (size_t)nacc * STRESS_SLOTS) +
+         align256(sizeof(float2) * (size_t)padded_points(n) * np) +
+         align256(sizeof(float) * (size_t)n * k) +
+         (det ? align256(sizeof(float) * part_floats(n, k)) : 0);
+}
+
+static IterWs carve(void* ws, int64_t n, int k, int nacc, bool det) {
   IterWs w;
   char* p = reinterpret_cast<char*>(ws);
   w.err = reinterpret_cast<unsigned*>(p);
   p += WS_HEADER;
   w.acc = reinterpret_cast<double*>(p);
-  p += align256(sizeof(double) * (size_t)nacc);
+  p += align256(sizeof(double) * (size_t)nacc * STRESS_SLOTS);
   w.P = reinterpret_cast<float2*>(p);
   p += align256(sizeof(float2) * (size_t)padded_points(n) * (k * (k - 1) / 2));
   w.h = reinterpret_cast<float*>(p);
+  p += align256(sizeof(float) * (size_t)n * k);
+  w.part = det ? reinterpret_cast<float*>(p) : nullptr;
   return w;
 }
 
@@ -1142,8 +1242,8 @@ static void update(int k, float* Y, int64_t n, float2* P, float* h, float scale,
 
 template <int K, bool FWD>
 static void launch_full(const IterParams& Q, cudaStream_t s) {
-  const int64_t blocks = (Q.n + 7) / 8;
-  const unsigned g = (unsigned)(blocks < 65535 * 8 ? blocks : 65535 * 8);
+  const int64_t blocks = (Q.n + 7) / 8;  // a warp per row, rows grid-strided
+  const unsigned g = (unsigned)(blocks < STRESS_SLOTS ? blocks : STRESS_SLOTS);
   gini_count_launch(1);
   k_full<K, FWD><<<g, 256, 0, s>>>(Q);
 }
@@ -1163,7 +1263,9 @@ static void full_k(int k, const IterParams& Q, cudaStream_t s) {
 
 template <int K, int DT, bool GRAD, bool GK = false>
 static void launch_fusedk(unsigned g, const IterParams& Q, int64_t ntiles, cudaStream_t s) {
-  const size_t smem = sizeof(FusedKSmem<K>);
+  // deterministic mode: per-warp column sums after the staged points
+  const size_t smem = sizeof(FusedKSmem<K>) +
+                      (GRAD && Q.part ? sizeof(float) * (FUSED_THREADS / 32) * TILE * K : 0);
   if (smem + 1024 > 48 * 1024)  // plus the kernel's static shared memory
     cudaFuncSetAttribute(k_fusedk<K, DT, GRAD, GK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
@@ -1174,7 +1276,7 @@ static void launch_fusedk(unsigned g, const IterParams& Q, int64_t ntiles, cudaS
 template <int DT, bool GRAD>
 static void launch_fused_dt(int k, const IterParams& Q, cudaStream_t s) {
   const int64_t ntiles = Q.tiles * (Q.tiles + 1) / 2;
-  const int64_t cap = (int64_t)sm_count() * 4;
+  const int64_t cap = std::min<int64_t>((int64_t)sm_count() * 4, STRESS_SLOTS);
   const unsigned g = (unsigned)(ntiles < cap ? ntiles : cap);
   if (!scalar2_path(k, Q.metric, Q.loss)) {
     switch (k) {
@@ -1204,7 +1306,7 @@ static void launch_fused_dt(int k, const IterParams& Q, cudaStream_t s) {
             per_sm < 1)
           per_sm = 1;
       }
-      const int64_t cap2 = (int64_t)sm_count() * per_sm;
+      const int64_t cap2 = std::min<int64_t>((int64_t)sm_count() * per_sm, STRESS_SLOTS);
       const unsigned g2 = (unsigned)(ntiles < cap2 ? ntiles : cap2);
       gini_count_launch(1);
       k_fused2<DT, GRAD><<<g2, PIPE_THREADS, C::smem, s>>>(Q, ntiles);
@@ -1229,8 +1331,10 @@ static void launch_fused(int k, int dtype, const IterParams& Q, cudaStream_t s) 
   }
 }
 
-// One pass: stress into *acc (and h if grad).  dtype_eff lets a BF16X2 matrix
-// be read through its hi plane only.
+// One pass: stress into the slots at Q.stress (and h if grad).  dtype_eff lets a
+// BF16X2 matrix be read through its hi plane only.  In deterministic mode the
+// fused kernels write per-tile partials and k_det_reduce forms h from them;
+// the plain form's adjoint writes each h_i from one warp already.
 static void one_pass(int k, int layout, int dtype_eff, bool grad, const IterParams& Q,
                      cudaStream_t s) {
   if (layout == GINI_LAYOUT_FULL) {
@@ -1238,6 +1342,11 @@ static void one_pass(int k, int layout, int dtype_eff, bool grad, const IterPara
     if (grad) full_k<false>(k, Q, s);
   } else if (grad) {
     launch_fused<true>(k, dtype_eff, Q, s);
+    if (Q.part) {
+      const int kp = scalar2_path(k, Q.metric, Q.loss) ? 1 : k;
+      gini_count_launch(1);
+      k_det_reduce<<<(unsigned)Q.tiles, 8 * TILE, 0, s>>>(Q.part, Q.n, Q.tiles, kp, Q.h);
+    }
   } else {
     launch_fused<false>(k, dtype_eff, Q, s);
   }
@@ -1256,6 +1365,7 @@ static IterParams make_params(int64_t n, int k, double nu, const float* Y, const
   Q.plane = gini_tiled_elems(n);
   Q.h = w.h;
   Q.stress = w.acc;
+  Q.part = w.part;
   Q.tab = make_tab(k, nu);
   Q.err = w.err;
   return Q;
@@ -1272,19 +1382,21 @@ extern "C" int gini_stress_grad_ex(const float* Y_dev, int64_t n, int k, double 
   if (loss != GINI_LOSS_KRUSKAL && loss != GINI_LOSS_SAMMON) return GINI_EINVAL;
   int st = check_common(n, k, nu, delta_dev, layout, dtype, ldd, col_scale_dev, norm);
   if (st != GINI_OK) return st;
-  if (ws_bytes < gini_workspace_size(GINI_OP_STRESS, n, 0, k, 0)) return GINI_ENOMEM;
+  const bool det = gini_get_deterministic() && layout == GINI_LAYOUT_TILED && grad_dev;
+  if (ws_bytes < gini_workspace_size(det ? GINI_OP_STRESS_DET : GINI_OP_STRESS, n, 0, k, 0))
+    return GINI_ENOMEM;
   cudaStream_t s = (cudaStream_t)stream;
-  IterWs w = carve(ws, n, k, 1);
+  IterWs w = carve(ws, n, k, 1, det);
   IterParams Q = make_params(n, k, nu, Y_dev, delta_dev, ldd, col_scale_dev, w);
   Q.metric = metric;
   Q.loss = loss;
-  cudaError_t e = cudaMemsetAsync(w.acc, 0, sizeof(double), s);
+  cudaError_t e = cudaMemsetAsync(w.acc, 0, sizeof(double) * STRESS_SLOTS, s);
   if (e == cudaSuccess && grad_dev) e = cudaMemsetAsync(w.h, 0, sizeof(float) * n * k, s);
   if (e != cudaSuccess) { gini_set_cuda_error(e); return GINI_ECUDA; }
   prep(k, Y_dev, n, w.P, w.err, s);
   one_pass(k, layout, dtype, grad_dev != nullptr, Q, s);
   gini_count_launch(grad_dev ? 2 : 1);
-  k_finalize_stress<<<1, 32, 0, s>>>(w.acc, 1, 1.0 / norm, nullptr, stress_dev);
+  k_finalize_stress<<<1, 32, 0, s>>>(w.acc, 1, 1.0 / norm, nullptr, stress_dev);  // one warp
   if (grad_dev)
     k_finalize_grad<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
         w.h, n, k, (float)(2.0 / norm), Q.tab.c2, scalar2_path(k, metric, loss), grad_dev);
@@ -1312,17 +1424,20 @@ extern "C" int gini_mds_fit(const gini_fit_args* a, void* ws, size_t ws_bytes, v
     return GINI_EINVAL;
   if (a->metric != GINI_METRIC_GINI && a->metric != GINI_METRIC_EUCLID) return GINI_EINVAL;
   if (a->loss != GINI_LOSS_KRUSKAL && a->loss != GINI_LOSS_SAMMON) return GINI_EINVAL;
-  if (ws_bytes < gini_workspace_size(GINI_OP_FIT, a->n, 0, a->k, a->iters)) return GINI_ENOMEM;
+  const bool det = (a->deterministic || gini_get_deterministic()) &&
+                   a->layout == GINI_LAYOUT_TILED && a->iters > 0;
+  if (ws_bytes < gini_workspace_size(det ? GINI_OP_FIT_DET : GINI_OP_FIT, a->n, 0, a->k, a->iters))
+    return GINI_ENOMEM;
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t n = a->n;
   const int k = a->k;
   const int T = a->iters;
-  IterWs w = carve(ws, n, k, T + 1);
+  IterWs w = carve(ws, n, k, T + 1, det);
   IterParams Q = make_params(n, k, a->nu, a->Y_dev, a->delta_dev, a->ldd, a->col_scale_dev, w);
   Q.metric = a->metric;
   Q.loss = a->loss;
   const bool sc2 = scalar2_path(k, a->metric, a->loss);
-  cudaError_t e = cudaMemsetAsync(w.acc, 0, sizeof(double) * (size_t)(T + 1), s);
+  cudaError_t e = cudaMemsetAsync(w.acc, 0, sizeof(double) * (size_t)(T + 1) * STRESS_SLOTS, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(w.h, 0, sizeof(float) * n * k, s);
   if (e != cudaSuccess) { gini_set_cuda_error(e); return GINI_ECUDA; }
   prep(k, a->Y_dev, n, w.P, w.err, s);
@@ -1331,15 +1446,15 @@ extern "C" int gini_mds_fit(const gini_fit_args* a, void* ws, size_t ws_bytes, v
   for (int t = 0; t < T; ++t) {
     int dt = a->dtype;
     if (dt == GINI_BF16X2 && a->layout == GINI_LAYOUT_TILED && t < polish_from) dt = GINI_BF16;
-    Q.stress = w.acc + t;
+    Q.stress = w.acc + (size_t)t * STRESS_SLOTS;
     one_pass(k, a->layout, dt, true, Q, s);
     update(k, a->Y_dev, n, w.P, w.h, scale, Q.tab.c2, sc2, w.err, s);
   }
-  Q.stress = w.acc + T;
+  Q.stress = w.acc + (size_t)T * STRESS_SLOTS;
   one_pass(k, a->layout, a->dtype, false, Q, s);
   gini_count_launch(1);
-  k_finalize_stress<<<1, 256, 0, s>>>(w.acc, T + 1, 1.0 / a->sum_delta2, a->history_dev,
-                                      a->final_stress_dev);
+  k_finalize_stress<<<(unsigned)((T + 1 + 7) / 8), 256, 0, s>>>(
+      w.acc, T + 1, 1.0 / a->sum_delta2, a->history_dev, a->final_stress_dev);
   e = cudaGetLastError();
   if (e != cudaSuccess) { gini_set_cuda_error(e); return GINI_ECUDA; }
   return GINI_OK;

@@ -40,7 +40,7 @@ def test_library_exports_every_declared_symbol(L):
 
 
 def test_constants(L):
-    assert L.gini_version() == 1
+    assert L.gini_version() == 2
     B = L.gini_tile_size()
     assert B == 128
     for n in (2, 127, 128, 129, 20000):
@@ -49,6 +49,12 @@ def test_constants(L):
     assert L.gini_workspace_size(0, 10, 5, 0, 0) >= 256
     assert L.gini_workspace_size(3, 1000, 0, 2, 50) > L.gini_workspace_size(2, 1000, 0, 2, 0)
     assert L.gini_workspace_size(99, 1, 1, 1, 1) == 0
+    # deterministic mode: per-tile gradient partials, 2 x 128 x k floats per tile
+    for n, k in ((1000, 2), (300, 3)):
+        T = -(-n // B)
+        extra = L.gini_workspace_size(5, n, 0, k, 50) - L.gini_workspace_size(3, n, 0, k, 50)
+        assert extra >= T * (T + 1) // 2 * 2 * B * k * 4
+        assert L.gini_workspace_size(4, n, 0, k, 0) > L.gini_workspace_size(2, n, 0, k, 0)
     assert b"EINVAL" in L.gini_status_str(1)
 
 
@@ -118,3 +124,16 @@ def test_misaligned_workspace_is_rejected_on_the_host(L):
     assert L.gini_distance_correlations(data, 100, 4, 4, data, 2, 1, data, ws, big,
                                         None) == EINVAL
     assert L.gini_silhouette(data, 100, 2, data, 2, data, ws, big, None) == EINVAL
+
+
+def test_deterministic_mode_is_per_thread(L):
+    import threading
+    assert L.gini_get_deterministic() == 0
+    L.gini_set_deterministic(1)
+    seen = []
+    t = threading.Thread(target=lambda: seen.append(L.gini_get_deterministic()))
+    t.start()
+    t.join()
+    assert L.gini_get_deterministic() == 1 and seen == [0]
+    L.gini_set_deterministic(0)
+    assert L.gini_get_deterministic() == 0

@@ -84,3 +84,47 @@ def test_fullsize_gradient_sampled_rows(G, full):
     gref = orc.grad_rows(Y.astype(np.float64), nu, Drows, rows, 1.0)
     err = np.max(np.abs(g.cpu().numpy()[rows] - gref))
     assert err <= 1e-5 * np.abs(gref).max(), err / np.abs(gref).max()
+
+
+def test_fullsize_deterministic_fit_repeats_and_resumes(G, full):
+    # The benchmark's fit (200 fused iterations, tiled FP32) in deterministic
+    # mode: two runs give the same bits, and 100 + 100 iterations from the
+    # fit's own Y_100 give the same Y_200 and S(Y_200) as 200 in one call.
+    w, X, Xd, D, sd2 = full
+    n, k, nu, T = w["n"], w["k"], 2.0, w["iters"]
+    Y0 = torch.from_numpy(wl.y_init(n, k, seed=w["seed"] + 1000)).cuda()
+    eta = G.default_step(n, k, nu, sd2)
+    Ya, ha, Sa = G.gini_mds_fit(Y0, nu, D, eta, T, deterministic=True)
+    Yb, hb, Sb = G.gini_mds_fit(Y0, nu, D, eta, T, deterministic=True)
+    assert torch.equal(Ya, Yb) and torch.equal(ha, hb) and float(Sa) == float(Sb)
+    Y1, _, _ = G.gini_mds_fit(Y0, nu, D, eta, T // 2, deterministic=True)
+    Y2, _, S2 = G.gini_mds_fit(Y1, nu, D, eta, T - T // 2, deterministic=True)
+    assert torch.equal(Y2, Ya) and float(S2) == float(Sa)
+
+
+def test_fullsize_gradient_rows_at_the_fits_scale(G, full):
+    # Near the end of a fit the residuals d - delta are small next to d and
+    # delta, which is where cancellation would show.  The evaluation point is
+    # built on the host: the seeded Y0 scaled by the factor that best matches
+    # the embedding distances to the dissimilarities over a sample of pairs
+    # (both from the oracle), so no output of the CUDA path feeds the oracle.
+    w, X, Xd, D, _ = full
+    n, k, nu = w["n"], w["k"], 2.0
+    Y0 = wl.y_init(n, k, seed=w["seed"] + 1000).astype(np.float64)
+    rng = np.random.default_rng(20002)
+    I = rng.integers(0, n, 3000)
+    J = (I + 1 + rng.integers(0, n - 1, 3000)) % n
+    dl = orc.delta_pairs(X, [nu], I, J)[:, 0]
+    u = Y0[:, 0] - Y0[:, 1]
+    d = 2.0 ** (1.0 - nu) * np.abs(u[I] - u[J])  # k = 2 closed form of the pseudo-distance
+    alpha = float(np.dot(d, dl) / np.dot(d, d))
+    Y = (alpha * Y0).astype(np.float32)
+    Dg = G.Dissimilarity(D.data, n, "tiled", "f32", 1.0)
+    _, g = G.gini_stress_grad(torch.from_numpy(Y).cuda(), nu, Dg)
+    rows = np.array([3, 4321, 15000, n - 2])
+    Ir = np.repeat(rows, n)
+    Jr = np.tile(np.arange(n), len(rows))
+    Drows = orc.delta_pairs(X, [nu], Ir, Jr)[:, 0].reshape(len(rows), n)
+    gref = orc.grad_rows(Y.astype(np.float64), nu, Drows, rows, 1.0)
+    err = np.max(np.abs(g.cpu().numpy()[rows] - gref))
+    assert err <= 1e-5 * np.abs(gref).max(), err / np.abs(gref).max()
