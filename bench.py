@@ -2,19 +2,23 @@
 
 One step = one whole Gini-MDS fit of the image-like workload (n = 20,000
 points, p = 784, k = 2, nu = 2, T = 200): the Delta build (sort of every pair's
-difference vector, midrank weights, BF16 hi+lo tiled store, FP64 sum of
-squares) followed by 200 fused stress+adjoint iterations (BF16 hi plane, the
-last 40 reading hi+lo) and the final FP64 stress.  Inputs are resident in HBM
-when the timed region starts; L2 is flushed between steps.
+difference vector, midrank weights, tiled FP32 store by default -- see --form,
+exact FP64 sum of squares) followed by 200 fused stress+adjoint iterations and
+the final FP64 stress.  Inputs are resident in HBM when the timed region
+starts; L2 is flushed between steps.
 
   value   = iterations per second of whole fits (T * steps / time of the steps,
             each step including its Delta build)
   e2e     = the same through the public host API (host X and Y0 copied in,
             Y_T and S(Y_T) copied out, inside the timed region)
 
-Also reported: the Delta build on its own (useful TFLOP/s, ranked elements/s),
-the iteration phase on its own, and the plain FP32 form (full square FP32
-Delta, separate forward and adjoint kernels) at the same configuration.
+Also reported on the same line: the Delta build on its own (useful TFLOP/s,
+ranked elements/s), the iteration phase on its own, the plain FP32 form (full
+square FP32 Delta, separate forward and adjoint kernels), every tiled storage
+form's iteration phase, the deterministic mode's fit against the plain form,
+the nu-grid build of the n = 2,000 image workload, and the batched
+configuration (64 UCI-sized problems x 8 nu x 8 restarts, one graph per fit
+batch).
 
 --impl reference times the FP64 CPU oracle on a bounded sample of the same
 workload and extrapolates (there is no reference implementation to run).
@@ -55,6 +59,8 @@ def _args():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-form comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end run")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the nu-grid build and the batched configuration")
     ap.add_argument("--form", default="f32", choices=list(FORMS),
                     help="storage of Delta in the timed fits")
     return ap.parse_args()
@@ -308,6 +314,11 @@ def run_ours(args, rank, local, world):
     if not args.no_plain and rank == 0:
         out["plain_fp32"], out["variants"] = _plain_and_variants(G, X, Y0, n, k, nu, T, stream,
                                                                  final_stress, P)
+    if not args.no_extra and rank == 0:
+        out["nu_grid_build"] = _nu_grid_build(G, dev, stream)
+        del X
+        torch.cuda.empty_cache()
+        out["batched"] = _batched_summary(G, dev, stream, steps=2)
     if not args.no_e2e:
         out["e2e"] = _e2e(G, X_host, Y0_host, n, p, k, nu, T, args, world)
     if rank == 0 and not args.no_cpu:
@@ -370,9 +381,32 @@ def _plain_and_variants(G, X, Y0, n, k, nu, T, stream, chosen_final, P):
                           "not_worse_than_plain_1e-4": float(fv) <= f * (1 + 1e-4),
                           "speedup_vs_plain": round(it / itv, 3)}
         del Dv
+    # the same fit in deterministic mode (fixed-order gradient reductions),
+    # twice: its final stress against the plain form's is then a fixed number
+    Dt = G.gini_pack(D, "f32")
+    G.gini_mds_fit(Y0, nu, Dt, eta, 5, history=False, check_errors=False, deterministic=True)
+    dets = []
+    for _ in range(2):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        Yd, _, fd = G.gini_mds_fit(Y0, nu, Dt, eta, T, history=False, check_errors=False,
+                                   deterministic=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        dets.append((e0.elapsed_time(e1) / (T + 1), Yd.clone(), float(fd)))
+    itd, fd = dets[0][0], dets[0][2]
+    variants["f32_deterministic"] = {
+        "iter_ms": round(itd, 5), "iters_per_s": round(1e3 / itd, 1),
+        "achieved_gbs": round(P * 4.0 / (itd / 1e3) / 1e9, 1),
+        "final_stress": fd,
+        "final_stress_rel_diff_vs_plain": abs(fd - f) / f,
+        "final_ks_rel_diff_vs_plain": abs(math.sqrt(fd) - math.sqrt(f)) / math.sqrt(f),
+        "equal_final_stress_1e-4": abs(fd - f) <= 1e-4 * f,
+        "repeat_bit_identical": bool(torch.equal(dets[0][1], dets[1][1])) and dets[1][2] == fd,
+        "note": "plain form and this one are both deterministic: the gap is the same every run"}
     # a k = 3 embedding on the same Delta (tiled FP32; the generic fused kernel)
     from paper_2605_25124_gb300 import workloads as wl
-    Dt = G.gini_pack(D, "f32")
     Y3 = torch.from_numpy(wl.y_init(n, 3, seed=4242)).to(Y0.device)
     eta3 = G.default_step(n, 3, nu, D.sum_delta2, 1.0)
     G.gini_mds_fit(Y3, nu, Dt, eta3, 5, history=False, check_errors=False)
@@ -391,6 +425,70 @@ def _plain_and_variants(G, X, Y0, n, k, nu, T, stream, chosen_final, P):
     del mats, D
     torch.cuda.empty_cache()
     return plain, variants
+
+
+def _nu_grid_build(G, dev, stream):
+    """Delta of the n = 2,000 image workload for nu in {1.5, 2, 3} from one sort
+    per pair (the non-affine weights' cell-key kernel), and nu = 1.5 alone."""
+    import torch
+    from paper_2605_25124_gb300 import workloads as wl
+    name = "image-n2000-p784"
+    w = wl.WORKLOADS[name]
+    X = torch.from_numpy(wl.make_X(name)).to(dev)
+    res = {"workload": name}
+    for key, nus in (("nu_1.5_2_3_ms", w["nu"]), ("nu_1.5_ms", [1.5])):
+        for _ in range(2):
+            G.gini_dist(X, nus, layout="tiled", dtype="f32", check_errors=False)
+        ts = []
+        for _ in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            G.gini_dist(X, nus, layout="tiled", dtype="f32", check_errors=False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        res[key] = round(statistics.median(ts), 3)
+    P = w["n"] * (w["n"] - 1) // 2
+    res["ranked_elements_per_s_nu_1.5"] = float(f"{P * w['p'] / (res['nu_1.5_ms'] / 1e3):.4e}")
+    return res
+
+
+def _batched_summary(G, dev, stream, steps=2):
+    """The batched configuration: 64 UCI-sized problems x 8 nu x 8 restarts,
+    k = 2, T = 200, one graph per fit batch (each step includes the Delta
+    builds); the first call autotunes and captures the graph."""
+    import numpy as np
+    import torch
+    from paper_2605_25124_gb300 import workloads as wl
+    name = "uci-batch-64"
+    w = wl.WORKLOADS[name]
+    Xs_host = wl.uci_like_batch(w["n_problems"], w["seed"])
+    R, T, nus = w["restarts"], w["iters"], [float(v) for v in w["nu"]]
+    Xs = [torch.from_numpy(Xh).to(dev) for Xh in Xs_host]
+    ns = [Xh.shape[0] for Xh in Xs_host]
+    Y0 = torch.from_numpy(np.concatenate([wl.y_init(R * n, 2, seed=w["seed"] + 1000 + q).reshape(-1)
+                                          for q, n in enumerate(ns)])).to(dev)
+    out = G.gini_fit_batched(Xs, nus, R, T, Y0, check_errors=False)
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = G.gini_fit_batched(Xs, nus, R, T, Y0, check_errors=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    G.workspace(dev).check()
+    nfits = len(ns) * len(nus) * R
+    pairs = sum(n * (n - 1) // 2 for n in ns) * len(nus)
+    ms = statistics.mean(times)
+    return {"workload": name, "fits": nfits, "iters": T, "ms_per_batch": round(ms, 3),
+            "fit_iters_per_s": round(nfits * T / (ms / 1e3), 1),
+            "delta_pairs_all_nu": pairs,
+            "achieved_delta_gbs": round(pairs * 4 * T / (ms / 1e3) / 1e9, 1),
+            "tuned_rows_x100_plus_ctas_per_sm": out["tuned"],
+            "note": "each batch includes its 64 Delta builds (8 nu from one sort per pair)"}
 
 
 def _e2e(G, X_host, Y0_host, n, p, k, nu, T, args, world):

@@ -217,11 +217,10 @@ int gini_stress_grad(const float* Y_dev, int64_t n, int k, double nu, const void
 
 /* gini_stress_grad for callers that cannot allocate device memory.  The paper
  * has no counterpart; this is a library service.  Some callers may not call
- * cudaMalloc at all: code recording a CUDA graph (allocation is not allowed
- * while a stream is being captured), plugins whose host application owns every
- * byte of device memory through its own pool, and latency-bound loops that
- * cannot afford the device-wide synchronisation an allocation or free implies.
- * They pass inputs and outputs exactly as for gini_stress_grad, but no
+ * cudaMalloc at all: plugins whose host application owns every byte of device
+ * memory through its own pool, and real-time or latency-bound loops that
+ * cannot afford the device-wide synchronisation that cudaMalloc and cudaFree
+ * imply.  They pass inputs and outputs exactly as for gini_stress_grad, but no
  * workspace: the scratch space is a fixed 8 MiB array inside the library, which
  * every GPU that loads the library holds until the process exits.
  *   - Sizes whose gini_workspace_size(GINI_OP_STRESS, n, 0, k, 0) exceeds 8 MiB

@@ -123,3 +123,45 @@ def test_batched_benchmark_configuration_sampled(G):
                 step_ref = y1 - y0
                 assert np.max(np.abs(step - step_ref)) <= (1e-5 * np.abs(step_ref).max()
                                                           + 2e-7 * np.abs(y0).max()), (q, v, r)
+
+
+def test_batched_ten_steps_against_the_oracle(G):
+    """Ten iterations of the benchmark's batch shape (64 UCI-sized problems x 8
+    nu x 8 restarts) for the three smallest problems and the smallest
+    integer-valued one: the stress history of every fit against the oracle's
+    fixed-step iterations, and Y_10.  The residual r = d - delta is formed in
+    FP32, so once a small problem's stress has dropped by orders of magnitude
+    its last digits go (an error of about 1e-7 of delta in r); the history is
+    therefore bounded against S(Y_0), the scale of those errors, and Y_10
+    against the distance the points moved."""
+    w = wl.WORKLOADS["uci-batch-64"]
+    Xs = wl.uci_like_batch(w["n_problems"], w["seed"])
+    R, nus, T = w["restarts"], [float(v) for v in w["nu"]], 10
+    ns = [X.shape[0] for X in Xs]
+    Y0s = [wl.y_init(R * n, 2, seed=w["seed"] + 1000 + q) for q, n in enumerate(ns)]
+    Xd = [torch.from_numpy(X).cuda() for X in Xs]
+    Y0 = torch.from_numpy(np.concatenate([y.reshape(-1) for y in Y0s])).cuda()
+    out = G.gini_fit_batched(Xd, nus, R, T, Y0, eta0=1.0, history=True)
+    Yb = out["Y"].cpu().numpy()
+    hist = out["history"].cpu().numpy()
+    sl = _slices(ns, len(nus), R)
+    order = np.argsort(ns)
+    ints = [q for q in order if q % 4 == 3]
+    picks = sorted({int(q) for q in order[:3]} | {int(ints[0])})
+    worst_h, worst_y = 0.0, 0.0
+    for q in picks:
+        n = ns[q]
+        D, sd2 = orc.delta(Xs[q], nus)
+        for v, nu in enumerate(nus):
+            eta = orc.default_step(n, 2, nu, sd2[v], 1.0)
+            for r in range(R):
+                y0 = Y0s[q][r * n:(r + 1) * n].astype(np.float64)
+                yT, h = orc.fit(D[v], nu, sd2[v], y0, eta, T)
+                worst_h = max(worst_h, np.max(np.abs(hist[:, q, v, r] - h)) / h[0])
+                a, b = sl[q, v, r]
+                moved = np.abs(yT - y0).max()
+                worst_y = max(worst_y, np.abs(Yb[a:b].reshape(n, 2) - yT).max() / moved)
+    print(f"10 batched steps: history max err / S(Y_0) {worst_h:.3e}, "
+          f"Y_10 max err / total move {worst_y:.3e}")
+    assert worst_h <= 1e-5
+    assert worst_y <= 1e-4

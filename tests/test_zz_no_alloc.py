@@ -1,6 +1,8 @@
 """gini_stress_grad_noalloc: the stress/gradient entry point for callers that
-may not allocate device memory (graph capture, host-owned memory pools,
-latency-bound loops), whose scratch space is a fixed array inside the library.
+may not allocate device memory (plugins whose host application owns every byte
+of device memory, real-time loops that cannot afford the synchronisation of
+cudaMalloc and cudaFree), whose scratch space is a fixed array inside the
+library.
 
 It is checked through the C ABI against gini_stress_grad with a caller
 workspace, on two calls in a row with different problems, at the tolerances
@@ -66,3 +68,20 @@ def test_noalloc_rejects_sizes_beyond_its_array(G):
     fake = ctypes.c_void_p(0x1000)  # never touched: the size check comes first
     assert L.gini_stress_grad_noalloc(fake, 2_000_000, 2, 2.0, fake, 1, 1, 0, None, 1.0,
                                       fake, fake, None) == GINI_ENOMEM
+
+
+def test_noalloc_reports_a_device_error_then_recovers(G):
+    # A NaN in Y is caught by the kernels (no fault) and reported as a NaN
+    # stress; the next call on the same array starts from a cleared error word
+    # and matches the workspace entry point.
+    nu = 2.0
+    X = wl.gaussian_outliers(400, 7, seed=405)
+    mats, _ = G.gini_dist(torch.from_numpy(X).cuda(), [nu], layout="tiled", dtype="f32")
+    Y = torch.from_numpy(wl.y_init(400, 2, seed=406, sd=1.0)).cuda()
+    Ybad = Y.clone()
+    Ybad[17, 1] = float("nan")
+    s_ref, g_ref, s_bad, _ = _both(G, Ybad, nu, mats[0])
+    assert np.isnan(s_bad)
+    s_ref, g_ref, s_new, g_new = _both(G, Y, nu, mats[0])
+    assert np.isfinite(s_new) and s_new == pytest.approx(s_ref, rel=1e-5)
+    assert np.max(np.abs(g_new - g_ref)) <= 1e-5 * np.abs(g_ref).max()
