@@ -96,7 +96,8 @@ typedef enum {
   GINI_OP_STRESS = 2,
   GINI_OP_FIT = 3,
   GINI_OP_STRESS_DET = 4,  /* GINI_OP_STRESS in deterministic mode (larger) */
-  GINI_OP_FIT_DET = 5      /* GINI_OP_FIT in deterministic mode (larger) */
+  GINI_OP_FIT_DET = 5,     /* GINI_OP_FIT in deterministic mode (larger) */
+  GINI_OP_DIST_FP8 = 6     /* GINI_OP_DIST with FP8 output (strip scratch) */
 } gini_op;
 
 /* Human-readable name of a status code (static string). */
@@ -168,22 +169,34 @@ int gini_rank(const float* v_dev, int64_t nseg, int64_t m, int64_t ld, int32_t* 
  *   X_dev      [n][ldx] float data, 2 <= n, 1 <= p <= 1024, ldx >= p
  *   nu_host    n_nu values, each > 1 and finite, 1 <= n_nu <= 8
  *   layout, dtype: GINI_LAYOUT_FULL with GINI_F32, or GINI_LAYOUT_TILED with
- *              GINI_F32, GINI_BF16 or GINI_BF16X2 (FP8 goes through gini_pack)
+ *              GINI_F32, GINI_BF16, GINI_BF16X2 or GINI_FP8E4M3
  *   delta_dev  output; matrix q starts at element q * nu_stride (in elements
  *              of the storage type; for BF16X2 the stride covers both planes)
  *   ldd        leading dimension of a FULL matrix (>= n); ignored for TILED
+ *   col_scale_dev  GINI_FP8E4M3 only (else NULL): n_nu x n floats out; matrix
+ *              q's column j holds col_scale[q n + j] = max_{i<j} |delta_ij| / 448
+ *              (1 for an all-zero column) and its tiles e4m3(delta_ij /
+ *              col_scale[q n + j]) (saturating), as gini_pack stores them.  The
+ *              matrix is built one strip of columns at a time into FP32 scratch
+ *              in the workspace (at least 4 n B n_nu bytes beyond
+ *              gini_workspace_size(GINI_OP_DIST, ...), B = gini_tile_size();
+ *              gini_workspace_size(GINI_OP_DIST_FP8, n, p, 0, 0) gives room for
+ *              all columns up to 128 MiB; a larger workspace gives wider
+ *              strips), so no n x n FP32 intermediate exists.
  *   sum_delta2_dev  n_nu doubles out: sum_{i<j} delta_ij^2 (FP32 values,
- *              FP64 sum), or NULL
- * The differences x_i - x_j are ranked in their exact order: each is the FP32
- * TwoSum pair (hi, lo), hi + lo = x_i - x_j, compared lexicographically (two
- * differences that round to one FP32 value are not a tie); the sums use hi.
- * For a single nu = 2 or nu = 3 the weights are affine in the rank
- * ((d/2) W_{d,3} = ((d-1)/d) (d/2) W_{d,2}) and FP32 keys give the same
- * result, so those cases sort FP32 values (about six times faster).
+ *              exact FP64 sum, the same bits on every run), or NULL
+ * The differences x_i - x_j are ranked in their exact order (a single nu = 2
+ * or nu = 3 needs no order among equal FP32 values: (d/2) W_{d,3} =
+ * ((d-1)/d) (d/2) W_{d,2} is affine in the rank).  Every other nu sorts 32-bit
+ * cell keys: twice the FP32 grid index of x_i - x_j when it is an FP32 value,
+ * the odd number between two grid indices otherwise; ties between two inexact
+ * differences in one FP32 cell are broken by their exact TwoSum pairs.  Sums
+ * use the cell end nearer zero (within one FP32 ulp of the difference).
  * Non-finite X is reported as GINI_ENONFINITE by gini_check. */
 int gini_dist(const float* X_dev, int64_t n, int64_t p, int64_t ldx, const double* nu_host,
               int n_nu, int layout, int dtype, void* delta_dev, int64_t ldd, int64_t nu_stride,
-              double* sum_delta2_dev, void* ws, size_t ws_bytes, void* stream);
+              float* col_scale_dev, double* sum_delta2_dev, void* ws, size_t ws_bytes,
+              void* stream);
 
 /* Converts a FULL F32 dissimilarity matrix (n x n, leading dimension ldd) to
  * the TILED layout of `dtype`.  For GINI_FP8E4M3, col_scale_dev (n floats,

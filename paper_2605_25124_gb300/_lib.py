@@ -16,7 +16,7 @@ DTYPES = {"f32": 0, "bf16": 1, "bf16x2": 2, "fp8": 3}
 METRICS = {"gini": 0, "euclid": 1}
 LOSSES = {"kruskal": 0, "sammon": 1}
 LAYOUTS = {"full": 0, "tiled": 1}
-OPS = {"rank": 0, "dist": 1, "stress": 2, "fit": 3, "stress_det": 4, "fit_det": 5}
+OPS = {"rank": 0, "dist": 1, "stress": 2, "fit": 3, "stress_det": 4, "fit_det": 5, "dist_fp8": 6}
 
 _c = ctypes
 _vp = _c.c_void_p
@@ -52,7 +52,8 @@ SIGNATURES = {
     "gini_check": (_c.c_int, [_vp, _vp]),
     "gini_rank": (_c.c_int, [_vp, _i64, _i64, _i64, _vp, _vp, _c.c_size_t, _vp]),
     "gini_dist": (_c.c_int, [_vp, _i64, _i64, _i64, _c.POINTER(_c.c_double), _c.c_int,
-                             _c.c_int, _c.c_int, _vp, _i64, _i64, _vp, _vp, _c.c_size_t, _vp]),
+                             _c.c_int, _c.c_int, _vp, _i64, _i64, _vp, _vp, _vp, _c.c_size_t,
+                             _vp]),
     "gini_pack": (_c.c_int, [_vp, _i64, _i64, _c.c_int, _vp, _vp, _vp]),
     "gini_stress_grad": (_c.c_int, [_vp, _i64, _c.c_int, _c.c_double, _vp, _c.c_int, _c.c_int,
                                     _i64, _vp, _c.c_double, _vp, _vp, _vp, _c.c_size_t, _vp]),

@@ -143,7 +143,9 @@ _TORCH_DT = {"f32": torch.float32, "bf16": torch.bfloat16, "bf16x2": torch.bfloa
 def gini_dist(X: torch.Tensor, nus: Sequence[float], layout: str = "full", dtype: str = "f32",
               ws: Optional[Workspace] = None, check_errors: bool = True):
     """Dissimilarity matrices for every nu: returns (list of Dissimilarity,
-    sum_delta2 tensor (n_nu,) float64 on the device)."""
+    sum_delta2 tensor (n_nu,) float64 on the device).  dtype "fp8" (tiled):
+    e4m3 with per-column scales, built strip by strip without an n x n
+    intermediate."""
     _require_cuda(X)
     assert X.dtype == torch.float32 and X.dim() == 2 and X.stride(1) == 1
     n, p = X.shape
@@ -157,17 +159,20 @@ def gini_dist(X: torch.Tensor, nus: Sequence[float], layout: str = "full", dtype
         stride = planes * tiled_elems(n)
         out = torch.empty((n_nu, stride), dtype=_TORCH_DT[dtype], device=X.device)
     sd2 = torch.zeros(n_nu, dtype=torch.float64, device=X.device)
+    fp8 = dtype == "fp8"
+    scale = torch.empty((n_nu, n), dtype=torch.float32, device=X.device) if fp8 else None
     ws = ws or workspace(X.device)
-    buf = ws.ensure(workspace_size("dist", n, p))
+    buf = ws.ensure(workspace_size("dist_fp8" if fp8 else "dist", n, p))
     nu_arr = (ctypes.c_double * n_nu)(*nus)
     st = lib().gini_dist(_ptr(X), n, p, X.stride(0), nu_arr, n_nu, LAYOUTS[layout],
-                         DTYPES[dtype], _ptr(out), n, stride, _ptr(sd2), _ptr(buf), buf.numel(),
-                         _stream())
+                         DTYPES[dtype], _ptr(out), n, stride, _ptr(scale), _ptr(sd2), _ptr(buf),
+                         buf.numel(), _stream())
     check(st, "gini_dist")
     if check_errors:
         ws.check()
     sums = sd2.cpu().tolist()
-    mats = [Dissimilarity(out[q], n, layout, dtype, sums[q]) for q in range(n_nu)]
+    mats = [Dissimilarity(out[q], n, layout, dtype, sums[q], scale[q] if fp8 else None)
+            for q in range(n_nu)]
     return mats, sd2
 
 

@@ -148,7 +148,8 @@ extern "C" int gini_alternating_nu(const float* X_dev, int64_t n, int64_t p, int
   for (int v0 = 0; v0 < nvals; v0 += 8) {
     const int nc = std::min(8, nvals - v0);
     int st = gini_dist(X_dev, n, p, ldx, nus.data() + v0, nc, GINI_LAYOUT_TILED, GINI_F32,
-                       delta + (size_t)v0 * plane, 0, plane, nullptr, ws, L.inner, stream);
+                       delta + (size_t)v0 * plane, 0, plane, nullptr, nullptr, ws, L.inner,
+                       stream);
     if (st != GINI_OK) return st;
   }
   for (int v = 0; v < nvals; ++v) {

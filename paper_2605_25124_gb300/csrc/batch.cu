@@ -587,7 +587,7 @@ extern "C" int gini_fit_batched(const gini_problem* probs, int nprob, const doub
     const int64_t plane = gini_tiled_elems(probs[q].n);
     const int st = gini_dist(probs[q].X_dev, probs[q].n, probs[q].p, probs[q].ldx, nu_host, n_nu,
                              GINI_LAYOUT_TILED, GINI_F32, w.delta + s0.delta_off, 0, plane,
-                             w.sd2 + (size_t)q * n_nu, w.wtab,
+                             nullptr, w.sd2 + (size_t)q * n_nu, w.wtab,
                              gini_workspace_size(GINI_OP_DIST, 2, pl.max_p, 0, 0), stream);
     if (st != GINI_OK) return st;
   }

@@ -58,7 +58,18 @@ extern "C" size_t gini_workspace_size(int op, int64_t n, int64_t m, int k, int i
     case GINI_OP_RANK: return WS_HEADER;
     case GINI_OP_DIST: {
       const int64_t mm = m < 1 ? 1 : m;
-      return WS_HEADER + 256 + (size_t)8 * (size_t)(2 * mm - 1) * sizeof(float);
+      return WS_HEADER + 256 + (((size_t)8 * (size_t)(2 * mm - 1) * sizeof(float) + 255) & ~(size_t)255);
+    }
+    case GINI_OP_DIST_FP8: {
+      // plus FP32 scratch for strips of columns of up to 8 matrices: all
+      // columns if that fits in 128 MiB, else as many whole tile columns as
+      // fit, at least one (a larger workspace gives wider strips)
+      const size_t rows = n < 2 ? 2 : (size_t)n;
+      const size_t per_col = sizeof(float) * rows * 8;
+      const size_t all = per_col * (size_t)(tiles_1d((int64_t)rows) * TILE);
+      size_t strip = all < ((size_t)128 << 20) ? all : ((size_t)128 << 20);
+      if (strip < per_col * TILE) strip = per_col * TILE;
+      return gini_workspace_size(GINI_OP_DIST, n, m, k, iters) + strip;
     }
     case GINI_OP_STRESS: return gini_iter_ws_bytes(n, k < 2 ? 2 : k, 1, 0);
     case GINI_OP_FIT: return gini_iter_ws_bytes(n, k < 2 ? 2 : k, (iters < 0 ? 0 : iters) + 1, 0);

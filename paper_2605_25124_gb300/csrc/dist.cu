@@ -40,6 +40,7 @@
 #include <math.h>
 #include <stdio.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "common.cuh"
@@ -49,6 +50,8 @@ namespace gini {
 
 constexpr int DIST_WARPS = 8;
 constexpr int NU_MAX = 8;
+// Internal layout of the FP8 output's column strips (see gini_dist).
+constexpr int LAYOUT_STRIP = 2;
 
 // Summary of X and the constants derived from it, kept in gini_dist's
 // workspace right after the error word.  The three extrema are gathered with
@@ -80,6 +83,7 @@ struct DistParams {
   double* sum_delta2;
   unsigned* err;
   DistState* st;
+  int64_t col_begin, col_end;  // columns j built by this launch (a strip for FP8 output)
   int cb;             // columns per CTA
   float affine_scale; // affine path: (d/2) W / (R - (d+1)/2), 1 for nu = 2, (d-1)/d for nu = 3
 };
@@ -104,6 +108,10 @@ __device__ __forceinline__ void store_delta(const DistParams& P, int q, int64_t 
     float* o = reinterpret_cast<float*>(P.out) + (int64_t)q * P.nu_stride;
     o[i * P.ldd + j] = d;
     o[j * P.ldd + i] = d;
+    return;
+  }
+  if (P.layout == LAYOUT_STRIP) {  // FP32 rows 0..n-1 of columns col_begin .. col_begin+ldd-1
+    reinterpret_cast<float*>(P.out)[(int64_t)q * P.nu_stride + i * P.ldd + (j - P.col_begin)] = d;
     return;
   }
   const int64_t idx = (int64_t)q * P.nu_stride + tiled_index(i, j, P.tiles);
@@ -158,7 +166,7 @@ __device__ __forceinline__ void dist_body(const DistParams& P) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int seg = lane / L, ls = lane % L;
   const int64_t row0 = (int64_t)blockIdx.y * DIST_WARPS;
-  const int64_t col0 = (int64_t)blockIdx.x * P.cb;
+  const int64_t col0 = P.col_begin + (int64_t)blockIdx.x * P.cb;
   // Nothing above the diagonal in this block (uniform exit, before any barrier).
   if (col0 + P.cb - 1 <= row0 || row0 >= P.n - 1) return;
   // The 64-bit network runs only where the pre-pass flagged the keyed kernel.
@@ -221,7 +229,7 @@ __device__ __forceinline__ void dist_body(const DistParams& P) {
 
   for (int64_t jb = col0; jb < col0 + P.cb; jb += G) {
     const int64_t j = jb + seg;
-    const bool active = row_ok && j > i && j < P.n;
+    const bool active = row_ok && j > i && j < P.col_end;
     if (!__any_sync(FULL_MASK, active)) continue;
     float acc[NQ];
 #pragma unroll
@@ -448,7 +456,7 @@ __device__ __forceinline__ void dist_keyed_body(const DistParams& P) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int seg = lane / L, ls = lane % L;
   const int64_t row0 = (int64_t)blockIdx.y * DIST_WARPS;
-  const int64_t col0 = (int64_t)blockIdx.x * P.cb;
+  const int64_t col0 = P.col_begin + (int64_t)blockIdx.x * P.cb;
   // Nothing above the diagonal in this block, or the 64-bit kernel's turn
   // (uniform exits, before any barrier).
   if (col0 + P.cb - 1 <= row0 || row0 >= P.n - 1) return;
@@ -489,7 +497,7 @@ __device__ __forceinline__ void dist_keyed_body(const DistParams& P) {
   const int pos0 = E * ls;
   for (int64_t jb = col0; jb < col0 + P.cb; jb += G) {
     const int64_t j = jb + seg;
-    const bool active = row_ok && j > i && j < P.n;
+    const bool active = row_ok && j > i && j < P.col_end;
     if (!__any_sync(FULL_MASK, active)) continue;
     float u[E];
 #pragma unroll
@@ -699,6 +707,52 @@ __global__ void k_zero_diag(float* D, int64_t n, int64_t ldd, int64_t nu_stride,
     for (int q = 0; q < n_nu; ++q) D[(int64_t)q * nu_stride + i * ldd + i] = 0.f;
 }
 
+// FP8 e4m3 output, built one strip of columns [c0, c1) at a time: the strip's
+// FP32 values (rows 0..n-1, entries i < j only) are in scratch; these kernels
+// take each column's max |delta| over i < j, turn it into the column's scale
+// max / 448 (1 for an all-zero column), and quantize the strip's tiles.
+// Block (x: 256 columns, y: 256 rows of the strip); bits of |delta| >= 0
+// order like the floats, so integer atomicMax gives the float maximum.
+__global__ void k_strip_colmax(const float* __restrict__ strip, int64_t n, int64_t w,
+                               int64_t c0, int64_t c1, unsigned* __restrict__ colmax) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c0 + c >= c1) return;
+  const int64_t j = c0 + c;
+  const int64_t i0 = (int64_t)blockIdx.y * 256;
+  unsigned m = 0;
+  for (int64_t i = i0; i < i0 + 256 && i < j; ++i)
+    m = max(m, __float_as_uint(fabsf(strip[i * w + c])));
+  if (m) atomicMax(colmax + j, m);
+}
+
+__global__ void k_strip_scale(unsigned* colmax_bits, int64_t c0, int64_t c1) {
+  const int64_t j = c0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= c1) return;
+  const float mx = __uint_as_float(colmax_bits[j]);
+  reinterpret_cast<float*>(colmax_bits)[j] = mx > 0.f ? mx / 448.f : 1.f;
+}
+
+// Block (x: tile of the strip, in row-major (I, J) order over J in the strip's
+// tile columns, y: 256-element slice of the tile); one thread per element.
+__global__ void k_strip_quant(const float* __restrict__ strip, int64_t n, int64_t w, int64_t c0,
+                              int64_t T, int64_t J0, int64_t nJ, const float* __restrict__ scale,
+                              __nv_fp8_storage_t* __restrict__ out) {
+  // tiles (I, J), J0 <= J < J0 + nJ, I <= J: enumerate J-major (column of
+  // tiles), I inside; t -> (I, J) by the running count (J + 1 tiles per column)
+  int64_t t = blockIdx.x, J = J0;
+  while (t > J) {
+    t -= J + 1;
+    ++J;
+  }
+  const int64_t I = t;
+  const int rc = (int)blockIdx.y * blockDim.x + threadIdx.x;
+  const int64_t i = I * TILE + rc / TILE, j = J * TILE + rc % TILE;
+  const float v = (i < n && j < n && i < j) ? strip[i * w + (j - c0)] : 0.f;
+  const float sc = (j < n) ? scale[j] : 1.f;
+  out[tile_offset(I, J, T) * (TILE * TILE) + rc] =
+      __nv_cvt_float_to_fp8(v / sc, __NV_SATFINITE, __NV_E4M3);
+}
+
 // KIND_KEYED + NQ: the keyed kernel with NQ nu slots.
 enum DistKind { KIND_AFFINE = 0, KIND_EXACT = 1, KIND_KEYED = 2 };
 
@@ -729,7 +783,9 @@ static cudaError_t launch_dist(const DistParams& P, cudaStream_t s) {
   // large n, or narrow segments with many pairs per warp.
   const bool wide = P.n >= 8192 || L < 8;
   Q.cb = G * (L >= 8 ? (wide ? 64 : 16) : (wide ? 16 : 4));
-  dim3 grid((unsigned)((P.n + Q.cb - 1) / Q.cb), (unsigned)((P.n + DIST_WARPS - 1) / DIST_WARPS));
+  const int64_t ncols = P.col_end - P.col_begin;
+  dim3 grid((unsigned)((ncols + Q.cb - 1) / Q.cb),
+            (unsigned)((std::min(P.n, P.col_end) + DIST_WARPS - 1) / DIST_WARPS));
   gini_count_launch(1);
   kern<<<grid, DIST_WARPS * 32, smem, s>>>(Q);
   return cudaGetLastError();
@@ -778,8 +834,8 @@ extern "C" void gini_set_cuda_error(cudaError_t e);
 
 extern "C" int gini_dist(const float* X_dev, int64_t n, int64_t p, int64_t ldx,
                          const double* nu_host, int n_nu, int layout, int dtype, void* delta_dev,
-                         int64_t ldd, int64_t nu_stride, double* sum_delta2_dev, void* ws,
-                         size_t ws_bytes, void* stream) {
+                         int64_t ldd, int64_t nu_stride, float* col_scale_dev,
+                         double* sum_delta2_dev, void* ws, size_t ws_bytes, void* stream) {
   if (!X_dev || !delta_dev || !nu_host || !ws) return GINI_EINVAL;
   if (ws_misaligned(ws)) return GINI_EINVAL;
   if (n < 2 || p < 1 || p > 1024 || ldx < p || n_nu < 1 || n_nu > NU_MAX) return GINI_EINVAL;
@@ -790,13 +846,18 @@ extern "C" int gini_dist(const float* X_dev, int64_t n, int64_t p, int64_t ldx,
     if (dtype != GINI_F32 || ldd < n) return GINI_EINVAL;
     if (n_nu > 1 && nu_stride < ldd * n) return GINI_EINVAL;
   } else if (layout == GINI_LAYOUT_TILED) {
-    if (dtype != GINI_F32 && dtype != GINI_BF16 && dtype != GINI_BF16X2) return GINI_EINVAL;
+    if (dtype < GINI_F32 || dtype > GINI_FP8E4M3) return GINI_EINVAL;
+    if (dtype == GINI_FP8E4M3 && !col_scale_dev) return GINI_EINVAL;
     const int64_t plane = gini_tiled_elems(n);
     if (n_nu > 1 && nu_stride < plane * (dtype == GINI_BF16X2 ? 2 : 1)) return GINI_EINVAL;
   } else {
     return GINI_EINVAL;
   }
-  if (ws_bytes < gini_workspace_size(GINI_OP_DIST, n, p, 0, 0)) return GINI_ENOMEM;
+  const bool fp8 = layout == GINI_LAYOUT_TILED && dtype == GINI_FP8E4M3;
+  const size_t ws_base = gini_workspace_size(GINI_OP_DIST, n, p, 0, 0);
+  // FP8 needs scratch for at least one tile column of every matrix
+  if (ws_bytes < ws_base + (fp8 ? sizeof(float) * (size_t)n * TILE * n_nu : 0))
+    return GINI_ENOMEM;
 
   cudaStream_t s = (cudaStream_t)stream;
   // workspace: error word | DistState | weight tables
@@ -844,15 +905,51 @@ extern "C" int gini_dist(const float* X_dev, int64_t n, int64_t p, int64_t ldx,
     P.layout = layout; P.dtype = dtype; P.out = delta_dev; P.ldd = ldd; P.nu_stride = nu_stride;
     P.tiles = tiles_1d(n); P.plane = gini_tiled_elems(n);
     P.sum_delta2 = sum_delta2_dev; P.err = err; P.st = st;
+    P.col_begin = 0; P.col_end = n;
     P.affine_scale = (affine && nu_host[0] == 3.0) ? (float)((double)(p - 1) / (double)p) : 1.f;
-    if (affine) {
-      e = dispatch_dist<KIND_AFFINE>(P, s);
-    } else {
+    auto build = [&](const DistParams& Q) -> cudaError_t {
+      if (affine) return dispatch_dist<KIND_AFFINE>(Q, s);
       // both launch; the pre-pass's flag lets exactly one of them do the work
-      e = n_nu == 1   ? dispatch_dist<KIND_KEYED + 1>(P, s)
-          : n_nu <= 4 ? dispatch_dist<KIND_KEYED + 4>(P, s)
-                      : dispatch_dist<KIND_KEYED + 8>(P, s);
-      if (e == cudaSuccess) e = dispatch_dist<KIND_EXACT>(P, s);
+      cudaError_t r = n_nu == 1   ? dispatch_dist<KIND_KEYED + 1>(Q, s)
+                      : n_nu <= 4 ? dispatch_dist<KIND_KEYED + 4>(Q, s)
+                                  : dispatch_dist<KIND_KEYED + 8>(Q, s);
+      return r == cudaSuccess ? dispatch_dist<KIND_EXACT>(Q, s) : r;
+    };
+    if (!fp8) {
+      e = build(P);
+    } else {
+      // FP8: strips of w columns (a multiple of the tile) built into FP32
+      // scratch, then each strip's column scales and its tiles of the output
+      float* strip = reinterpret_cast<float*>(reinterpret_cast<char*>(ws) + ws_base);
+      const size_t budget = ws_bytes - ws_base;
+      int64_t w = (int64_t)(budget / (sizeof(float) * (size_t)n * n_nu)) / TILE * TILE;
+      w = std::min(w, tiles_1d(n) * TILE);
+      if (w < TILE) return GINI_ENOMEM;
+      e = cudaMemsetAsync(col_scale_dev, 0, sizeof(float) * (size_t)n * n_nu, s);
+      const int64_t T = tiles_1d(n), plane = gini_tiled_elems(n);
+      for (int64_t c0 = 0; c0 < n && e == cudaSuccess; c0 += w) {
+        const int64_t c1 = std::min(n, c0 + w);
+        DistParams Q = P;
+        Q.layout = LAYOUT_STRIP; Q.out = strip; Q.ldd = w; Q.nu_stride = n * w;
+        Q.col_begin = c0; Q.col_end = c1;
+        e = build(Q);
+        const int64_t J0 = c0 / TILE, nJ = tiles_1d(c1) - J0;
+        int64_t ntile = 0;
+        for (int64_t J = J0; J < J0 + nJ; ++J) ntile += J + 1;
+        for (int q = 0; q < n_nu && e == cudaSuccess; ++q) {
+          const float* sq = strip + (int64_t)q * n * w;
+          unsigned* cm = reinterpret_cast<unsigned*>(col_scale_dev + (int64_t)q * n);
+          gini_count_launch(3);
+          k_strip_colmax<<<dim3((unsigned)((c1 - c0 + 255) / 256), (unsigned)((c1 + 255) / 256)),
+                           256, 0, s>>>(sq, n, w, c0, c1, cm);
+          k_strip_scale<<<(unsigned)((c1 - c0 + 255) / 256), 256, 0, s>>>(cm, c0, c1);
+          k_strip_quant<<<dim3((unsigned)ntile, TILE * TILE / 256), 256, 0, s>>>(
+              sq, n, w, c0, T, J0, nJ, col_scale_dev + (int64_t)q * n,
+              reinterpret_cast<__nv_fp8_storage_t*>(delta_dev) + (int64_t)q * nu_stride);
+          e = cudaGetLastError();
+        }
+        (void)plane;
+      }
     }
   }
   if (e == cudaSuccess && sum_delta2_dev) {

@@ -79,12 +79,12 @@ def test_host_side_validation(L):
     assert L.gini_rank(fake, 4, 8, 4, fake, ws, 1 << 20, None) == EINVAL
     assert L.gini_rank(None, 4, 8, 8, fake, ws, 1 << 20, None) == EINVAL
     # gini_dist: nu <= 1, n < 2, p > 1024, FULL needs F32, small workspace
-    assert L.gini_dist(fake, 10, 5, 5, bad_nu, 1, 0, 0, fake, 10, 100, None, ws, 1 << 20, None) == EINVAL
-    assert L.gini_dist(fake, 1, 5, 5, nu, 1, 0, 0, fake, 10, 100, None, ws, 1 << 20, None) == EINVAL
-    assert L.gini_dist(fake, 10, 1025, 1025, nu, 1, 0, 0, fake, 10, 100, None, ws, 1 << 20, None) == EINVAL
-    assert L.gini_dist(fake, 10, 5, 5, nu, 1, 0, 1, fake, 10, 100, None, ws, 1 << 20, None) == EINVAL
-    assert L.gini_dist(fake, 10, 5, 5, nu, 1, 1, 3, fake, 10, 100, None, ws, 1 << 20, None) == EINVAL
-    assert L.gini_dist(fake, 10, 5, 5, nu, 1, 0, 0, fake, 10, 100, None, ws, 8, None) == ENOMEM
+    assert L.gini_dist(fake, 10, 5, 5, bad_nu, 1, 0, 0, fake, 10, 100, None, None, ws, 1 << 20, None) == EINVAL
+    assert L.gini_dist(fake, 1, 5, 5, nu, 1, 0, 0, fake, 10, 100, None, None, ws, 1 << 20, None) == EINVAL
+    assert L.gini_dist(fake, 10, 1025, 1025, nu, 1, 0, 0, fake, 10, 100, None, None, ws, 1 << 20, None) == EINVAL
+    assert L.gini_dist(fake, 10, 5, 5, nu, 1, 0, 1, fake, 10, 100, None, None, ws, 1 << 20, None) == EINVAL
+    assert L.gini_dist(fake, 10, 5, 5, nu, 1, 1, 3, fake, 10, 100, None, None, ws, 1 << 20, None) == EINVAL
+    assert L.gini_dist(fake, 10, 5, 5, nu, 1, 0, 0, fake, 10, 100, None, None, ws, 8, None) == ENOMEM
     # gini_stress_grad: k = 1 and k > 8, nu <= 1, zero sum_delta2, unaligned tiled data
     args = lambda k, nu_, sd2, delta=fake, layout=0: (fake, 10, k, nu_, delta, layout, 0, 10, None,
                                                       sd2, fake, None, ws, 1 << 20, None)
@@ -110,7 +110,7 @@ def test_misaligned_workspace_is_rejected_on_the_host(L):
     data, ws = 0x10000000, 0x20000010  # ws 16-byte but not 256-byte aligned
     big = 1 << 40
     nu = (ctypes.c_double * 1)(2.0)
-    assert L.gini_dist(data, 100, 8, 8, nu, 1, 1, 0, data, 0, 0, None, ws, big, None) == EINVAL
+    assert L.gini_dist(data, 100, 8, 8, nu, 1, 1, 0, data, 0, 0, None, None, ws, big, None) == EINVAL
     assert L.gini_rank(data, 10, 8, 8, data, ws, big, None) == EINVAL
     assert L.gini_stress_grad(data, 100, 2, 2.0, data, 1, 0, 0, None, 1.0, data, data, ws, big,
                               None) == EINVAL

@@ -252,3 +252,60 @@ def test_delta_sum_of_squares_is_run_to_run_identical(G):
         a = [G.gini_dist(X, nus, layout="tiled", dtype="f32")[1].cpu().numpy() for _ in range(3)]
         for b in a[1:]:
             np.testing.assert_array_equal(a[0], b)
+
+
+def _e4m3_decode(q):
+    q = np.asarray(q).view(np.uint8)
+    s = np.where(q & 0x80, -1.0, 1.0)
+    e = (q >> 3) & 0xF
+    mant = (q & 7).astype(np.float64)
+    return s * np.where(e == 0, mant / 8 * 2.0 ** -6, (1 + mant / 8) * 2.0 ** (e.astype(np.float64) - 7))
+
+
+@pytest.mark.parametrize("strips", ["one", "many"])
+def test_delta_fp8_output_direct(G, strips):
+    # gini_dist writing e4m3 tiles with per-column scales itself: against the
+    # oracle at the e4m3 bound, and bit for bit against packing the FULL FP32
+    # build (same values, same scale rule).  "many": a workspace with room for
+    # one tile column of FP32 scratch, so the build runs strip by strip.
+    import ctypes
+    from paper_2605_25124_gb300._lib import DTYPES, LAYOUTS, OPS, lib
+    n, nus = 300, [1.6, 2.0]
+    X = wl.gaussian_outliers(n, 11, seed=5300)
+    ref, sref = orc.delta(X, nus)
+    Xd = torch.from_numpy(X).cuda()
+    L = lib()
+    plane = G.tiled_elems(n)
+    out = torch.zeros(2 * plane, dtype=torch.uint8, device="cuda")
+    scale = torch.empty(2 * n, dtype=torch.float32, device="cuda")
+    sd2 = torch.zeros(2, dtype=torch.float64, device="cuda")
+    base = L.gini_workspace_size(OPS["dist"], n, 11, 0, 0)
+    full = L.gini_workspace_size(OPS["dist_fp8"], n, 11, 0, 0)
+    nbytes = base + 4 * n * 128 * 2 if strips == "many" else full
+    assert nbytes <= full
+    ws = torch.zeros(nbytes, dtype=torch.uint8, device="cuda")
+    nu_arr = (ctypes.c_double * 2)(*nus)
+    p = lambda t: ctypes.c_void_p(t.data_ptr())
+    st = L.gini_dist(p(Xd), n, 11, 11, nu_arr, 2, LAYOUTS["tiled"], DTYPES["fp8"], p(out), 0,
+                     plane, p(scale), p(sd2), p(ws), nbytes,
+                     ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == 0
+    torch.cuda.synchronize()
+    iu = np.triu_indices(n, 1)
+    mats, _ = G.gini_dist(Xd, nus, layout="full")
+    for q in range(2):
+        sc = scale[q * n:(q + 1) * n].cpu().numpy()
+        got = untile(_e4m3_decode(out[q * plane:(q + 1) * plane].cpu().numpy()), n) * sc[None, :]
+        err = np.abs(got[iu] - ref[q][iu])
+        bound = 2.0 ** -4 * np.abs(ref[q][iu]) + 2.0 ** -10 * sc[iu[1]]
+        assert np.all(err <= bound + 1e-6)
+        colmax = np.max(np.triu(ref[q], 1), axis=0)
+        np.testing.assert_allclose(sc[1:], np.where(colmax[1:] > 0, colmax[1:] / 448, 1),
+                                   rtol=1e-5)
+        assert sd2[q].item() == pytest.approx(sref[q], rel=1e-6)
+        P = G.gini_pack(mats[q], "fp8")
+        assert torch.equal(P.col_scale, scale[q * n:(q + 1) * n])
+        assert torch.equal(P.data, out[q * plane:(q + 1) * plane])
+    # the Python binding's FP8 path and a stress evaluation on it
+    m8, _ = G.gini_dist(Xd, nus, layout="tiled", dtype="fp8")
+    assert torch.equal(m8[0].data, out[:plane]) and torch.equal(m8[0].col_scale, scale[:n])
