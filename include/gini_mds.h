@@ -158,7 +158,8 @@ int gini_check(void* ws, void* stream);
  *   rank2_dev [nseg][m] int32 out: rank2[s*m + a] = 2 R(v_a)
  *             = 2 #{b: v_b < v_a} + #{b: v_b == v_a} + 1  (exact integers;
  *             -0.0 and +0.0 are equal)
- * 1 <= m <= 1024, ld >= m.  NaN/Inf inputs are reported as GINI_ENONFINITE
+ * 1 <= m <= 8192 (above 1024 the segment is sorted in chunks and ranked by
+ * search), ld >= m.  NaN/Inf inputs are reported as GINI_ENONFINITE
  * by gini_check (their ranks are then unspecified). */
 int gini_rank(const float* v_dev, int64_t nseg, int64_t m, int64_t ld, int32_t* rank2_dev,
               void* ws, size_t ws_bytes, void* stream);
@@ -166,7 +167,9 @@ int gini_rank(const float* v_dev, int64_t nseg, int64_t m, int64_t ld, int32_t* 
 /* Dissimilarity matrices Delta_q = [Dbar_{G,nu_q}(x_i, x_j)] for every nu_q
  * (Section III-B; Algorithm 1, "Compute Gini pseudo-distances"), one sort of
  * each pair's difference vector serving all nu values.
- *   X_dev      [n][ldx] float data, 2 <= n, 1 <= p <= 1024, ldx >= p
+ *   X_dev      [n][ldx] float data, 2 <= n, 1 <= p <= 8192, ldx >= p (above
+ *              1024 one warp sorts each pair's vector in 1024-element chunks
+ *              and ranks by search, with n <= 65536)
  *   nu_host    n_nu values, each > 1 and finite, 1 <= n_nu <= 8
  *   layout, dtype: GINI_LAYOUT_FULL with GINI_F32, or GINI_LAYOUT_TILED with
  *              GINI_F32, GINI_BF16, GINI_BF16X2 or GINI_FP8E4M3
@@ -306,7 +309,7 @@ int gini_mds_fit(const gini_fit_args* args, void* ws, size_t ws_bytes, void* str
 typedef struct {
   const float* X_dev;  /* [n][ldx] float data */
   int64_t n;           /* points, 2 .. 524,280 */
-  int64_t p;           /* features, 1 .. 1024 */
+  int64_t p;           /* features, 1 .. 8192 */
   int64_t ldx;         /* >= p */
 } gini_problem;
 
@@ -386,7 +389,7 @@ size_t gini_alternating_nu_workspace_size(int64_t n, int64_t p, int k, int n_nu,
  * metric) or 1 (Euclidean),
  *   Kruskal: eta = eta0 sum delta^2 / (2 (n-1) c)
  *   Sammon:  eta = eta0 sum delta / (2 c max_i sum_{j: delta_ij > 0} 1/delta_ij).
- *   X_dev         n x p floats (p <= 1024), row stride ldx
+ *   X_dev         n x p floats (p <= 8192), row stride ldx
  *   nu_host       n_nu (1..64) grid values, each > 1; nu_start > 1
  *   k             2..8; metric gini_metric; loss gini_loss (Algorithm 2: Sammon)
  *   Y_dev         n x k floats, in: Y_0, out: the last round's fit

@@ -123,7 +123,7 @@ extern "C" int gini_alternating_nu(const float* X_dev, int64_t n, int64_t p, int
                                    size_t ws_bytes, void* stream) {
   if (!X_dev || !nu_host || !Y_dev || !nu_path_host || !ks_host || !ws) return GINI_EINVAL;
   if (ws_misaligned(ws)) return GINI_EINVAL;
-  if (n < 2 || p < 1 || p > 1024 || ldx < p || k < 2 || k > 8 || n_nu < 1 || n_nu > 64 ||
+  if (n < 2 || p < 1 || p > 8192 || ldx < p || k < 2 || k > 8 || n_nu < 1 || n_nu > 64 ||
       rounds < 1 || iters < 0)
     return GINI_EINVAL;
   if (metric != GINI_METRIC_GINI && metric != GINI_METRIC_EUCLID) return GINI_EINVAL;

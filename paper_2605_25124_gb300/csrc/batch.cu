@@ -570,7 +570,7 @@ extern "C" int gini_fit_batched(const gini_problem* probs, int nprob, const doub
     if (!(nu_host[v] > 1.0) || !isfinite(nu_host[v])) return GINI_EINVAL;
   for (int q = 0; q < nprob; ++q) {
     const gini_problem& pq = probs[q];
-    if (!pq.X_dev || pq.n < 2 || pq.n > 65535 * 8 || pq.p < 1 || pq.p > 1024 || pq.ldx < pq.p)
+    if (!pq.X_dev || pq.n < 2 || pq.n > 65535 * 8 || pq.p < 1 || pq.p > 8192 || pq.ldx < pq.p)
       return GINI_EINVAL;
   }
   BatchPlan pl = make_plan(probs, nprob, nu_host, n_nu, restarts, eta0);

@@ -753,6 +753,90 @@ __global__ void k_strip_quant(const float* __restrict__ strip, int64_t n, int64_
       __nv_cvt_float_to_fp8(v / sc, __NV_SATFINITE, __NV_E4M3);
 }
 
+// Vectors longer than one warp's registers (1024 < p <= 8192): one warp per
+// pair sorts the exact (hi, lo) keys of x_i - x_j chunk by chunk into shared
+// memory; every element's midrank then comes from binary searches in all
+// chunks (lt below, eq equal, itself included: first + last = 2 lt + eq - 1),
+// and it adds hi * T_q[first + last] for every nu (tables read from the
+// workspace through the cache).  Exact for every nu; the work per pair is
+// O(p log^2 1024 + p C log 1024) for C chunks.  CTA = LONG_WARPS pairs of one
+// row i: j = max(i + 1, col_begin) + LONG_WARPS x + warp.
+constexpr int LONG_WARPS = 2;
+
+__global__ void __launch_bounds__(LONG_WARPS * 32) k_dist_long(const DistParams P, int nchunk) {
+  extern __shared__ unsigned long long s_long[];  // [LONG_WARPS][nchunk][LONG_CHUNK_SLOTS]
+  __shared__ double s_sd2[LONG_WARPS][NU_MAX];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m = (int)P.m, tab_n = 2 * m - 1;
+  const int64_t i = blockIdx.y;
+  const int64_t j = std::max(i + 1, P.col_begin) + (int64_t)blockIdx.x * LONG_WARPS + warp;
+  const bool active = i < P.n - 1 && j < P.col_end;
+  unsigned long long* K = s_long + (size_t)warp * nchunk * LONG_CHUNK_SLOTS;
+  const float* xi = P.X + i * P.ldx;
+  const float* xj = P.X + (active ? j : i) * P.ldx;
+  if (active) {  // warp-uniform
+    for (int c = 0; c < nchunk; ++c) {
+      unsigned long long kv[32];
+#pragma unroll
+      for (int t = 0; t < 32; ++t) {
+        const int e = c * LONG_CHUNK + t * 32 + lane;
+        kv[t] = e < m ? exact_key(__ldg(xi + e), __ldg(xj + e)) : ~0ull;
+      }
+      long_sort_chunk(kv, lane, K + (size_t)c * LONG_CHUNK_SLOTS);
+    }
+    __syncwarp();
+    float acc[NU_MAX];
+#pragma unroll
+    for (int q = 0; q < NU_MAX; ++q) acc[q] = 0.f;
+    for (int e = lane; e < m; e += 32) {
+      const float a = __ldg(xi + e), b = __ldg(xj + e);
+      const unsigned long long k = exact_key(a, b);
+      int lt = 0, eq = 0;
+      for (int c = 0; c < nchunk; ++c)
+        long_count(K + (size_t)c * LONG_CHUNK_SLOTS, min(LONG_CHUNK, m - c * LONG_CHUNK), k, lt,
+                   eq);
+      const float hi = two_sum_canonical(a, -b).x;
+      const int idx = 2 * lt + eq - 1;
+#pragma unroll
+      for (int q = 0; q < NU_MAX; ++q)
+        if (q < P.n_nu) acc[q] = fmaf(hi, __ldg(P.wtab + (int64_t)q * tab_n + idx), acc[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < NU_MAX; ++q) {
+#pragma unroll
+      for (int o = 16; o >= 1; o >>= 1) acc[q] += __shfl_xor_sync(FULL_MASK, acc[q], o);
+    }
+    if (lane == 0) {
+      for (int q = 0; q < P.n_nu; ++q) {
+        store_delta(P, q, i, j, acc[q]);
+        s_sd2[warp][q] = (double)acc[q] * (double)acc[q];
+      }
+    }
+  } else if (lane == 0) {
+    for (int q = 0; q < NU_MAX; ++q) s_sd2[warp][q] = 0.0;
+  }
+  __syncthreads();
+  if (threadIdx.x < P.n_nu && P.sum_delta2) {
+    double sum = 0.0;
+    for (int w = 0; w < LONG_WARPS; ++w) sum += s_sd2[w][threadIdx.x];
+    add_exact128(P.st->sd2[threadIdx.x], sum, P.st->sd2_q);
+  }
+}
+
+static cudaError_t launch_dist_long(const DistParams& P, cudaStream_t s) {
+  const int nchunk = (int)((P.m + LONG_CHUNK - 1) / LONG_CHUNK);
+  const size_t smem = sizeof(unsigned long long) * LONG_WARPS * nchunk * LONG_CHUNK_SLOTS;
+  cudaError_t e = cudaFuncSetAttribute(k_dist_long, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  const int64_t rows = std::min(P.n, P.col_end) - 1;
+  const int64_t span = P.col_end - P.col_begin;
+  dim3 grid((unsigned)((span + LONG_WARPS - 1) / LONG_WARPS), (unsigned)rows);
+  gini_count_launch(1);
+  k_dist_long<<<grid, LONG_WARPS * 32, smem, s>>>(P, nchunk);
+  return cudaGetLastError();
+}
+
 // KIND_KEYED + NQ: the keyed kernel with NQ nu slots.
 enum DistKind { KIND_AFFINE = 0, KIND_EXACT = 1, KIND_KEYED = 2 };
 
@@ -838,8 +922,11 @@ extern "C" int gini_dist(const float* X_dev, int64_t n, int64_t p, int64_t ldx,
                          double* sum_delta2_dev, void* ws, size_t ws_bytes, void* stream) {
   if (!X_dev || !delta_dev || !nu_host || !ws) return GINI_EINVAL;
   if (ws_misaligned(ws)) return GINI_EINVAL;
-  if (n < 2 || p < 1 || p > 1024 || ldx < p || n_nu < 1 || n_nu > NU_MAX) return GINI_EINVAL;
+  if (n < 2 || p < 1 || p > (int64_t)LONG_CHUNK * LONG_MAX_CHUNKS || ldx < p || n_nu < 1 ||
+      n_nu > NU_MAX)
+    return GINI_EINVAL;
   if (n > (int64_t)65535 * DIST_WARPS) return GINI_EINVAL;  // grid.y = ceil(n / 8)
+  if (p > LONG_CHUNK && n > 65536) return GINI_EINVAL;      // long vectors: grid.y = n - 1
   for (int q = 0; q < n_nu; ++q)
     if (!(nu_host[q] > 1.0) || !isfinite(nu_host[q])) return GINI_EINVAL;
   if (layout == GINI_LAYOUT_FULL) {
@@ -869,7 +956,7 @@ extern "C" int gini_dist(const float* X_dev, int64_t n, int64_t p, int64_t ldx,
   // (d/2) W_{d,3}(R) = ((d-1)/d) (R - (d+1)/2) = ((d-1)/d) (d/2) W_{d,2}(R)
   const bool affine = (n_nu == 1 && (nu_host[0] == 2.0 || nu_host[0] == 3.0));
   const int tab_n = (int)(2 * p - 1);
-  if (!affine) {
+  if (!affine || p > LONG_CHUNK) {  // long vectors always read the table
     // T_q[idx] = (d/2) W_{d,nu_q}((idx + 2)/2), W(R) = ((R-1)/d)^{nu-1} - ((d-R)/d)^{nu-1}
     std::vector<float> tab((size_t)n_nu * tab_n);
     const double d = (double)p;
@@ -908,6 +995,7 @@ extern "C" int gini_dist(const float* X_dev, int64_t n, int64_t p, int64_t ldx,
     P.col_begin = 0; P.col_end = n;
     P.affine_scale = (affine && nu_host[0] == 3.0) ? (float)((double)(p - 1) / (double)p) : 1.f;
     auto build = [&](const DistParams& Q) -> cudaError_t {
+      if (p > LONG_CHUNK) return launch_dist_long(Q, s);
       if (affine) return dispatch_dist<KIND_AFFINE>(Q, s);
       // both launch; the pre-pass's flag lets exactly one of them do the work
       cudaError_t r = n_nu == 1   ? dispatch_dist<KIND_KEYED + 1>(Q, s)

@@ -1,9 +1,11 @@
 // Segmented midranks (Definition 1 with midpoint ranks for ties, Eq. (rank-ties)).
 //
-// A segment of m values is sorted as 64-bit keys (order-preserving bits of
-// the float in the high word, the element's index in the low word) by the
-// register bitonic network; tie runs are detected on the high word, and
+// A segment of m <= 1024 values is sorted as 64-bit keys (order-preserving
+// bits of the float in the high word, the element's index in the low word) by
+// the register bitonic network; tie runs are detected on the high word, and
 // 2R = first + last position of the run + 2 is scattered back to the index.
+// Longer segments (up to 8192) are sorted in chunks and ranked by search
+// (k_rank_long).
 #include "common.cuh"
 #include "sortnet.cuh"
 
@@ -58,6 +60,48 @@ k_rank(const float* __restrict__ v, int64_t nseg, int m, int64_t ld, int32_t* __
   }
 }
 
+// Segments longer than 1024: one warp per segment sorts the value keys
+// (ordered bits in the high word) chunk by chunk into shared memory, and each
+// element's 2R = 2 #{below} + #{equal, itself included} + 1 comes from
+// binary searches in every chunk.
+constexpr int RANK_LONG_WARPS = 2;
+
+__global__ void __launch_bounds__(RANK_LONG_WARPS * 32)
+k_rank_long(const float* __restrict__ v, int64_t nseg, int m, int64_t ld, int nchunk,
+            int32_t* __restrict__ out, unsigned* err) {
+  extern __shared__ unsigned long long s_rk[];  // [RANK_LONG_WARPS][nchunk][LONG_CHUNK_SLOTS]
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t sidx = (int64_t)blockIdx.x * RANK_LONG_WARPS + warp;
+  if (sidx >= nseg) return;  // warp-uniform; no CTA barrier below
+  unsigned long long* K = s_rk + (size_t)warp * nchunk * LONG_CHUNK_SLOTS;
+  const float* row = v + sidx * ld;
+  bool bad = false;
+  for (int c = 0; c < nchunk; ++c) {
+    unsigned long long kv[32];
+#pragma unroll
+    for (int t = 0; t < 32; ++t) {
+      const int e = c * LONG_CHUNK + t * 32 + lane;
+      if (e < m) {
+        const float x = row[e];
+        bad |= !isfinite(x);
+        kv[t] = (unsigned long long)ordered_bits(x) << 32;
+      } else {
+        kv[t] = ~0ull;
+      }
+    }
+    long_sort_chunk(kv, lane, K + (size_t)c * LONG_CHUNK_SLOTS);
+  }
+  if (__any_sync(FULL_MASK, bad) && lane == 0) raise_error(err, ERR_NONFINITE);
+  __syncwarp();
+  for (int e = lane; e < m; e += 32) {
+    const unsigned long long k = (unsigned long long)ordered_bits(row[e]) << 32;
+    int lt = 0, eq = 0;
+    for (int c = 0; c < nchunk; ++c)
+      long_count(K + (size_t)c * LONG_CHUNK_SLOTS, min(LONG_CHUNK, m - c * LONG_CHUNK), k, lt, eq);
+    out[sidx * m + e] = 2 * lt + eq + 1;
+  }
+}
+
 template <int E, int L>
 static cudaError_t launch_rank(const float* v, int64_t nseg, int m, int64_t ld, int32_t* out,
                                unsigned* err, cudaStream_t s) {
@@ -77,12 +121,13 @@ extern "C" void gini_set_cuda_error(cudaError_t e);
 
 extern "C" int gini_rank(const float* v_dev, int64_t nseg, int64_t m, int64_t ld,
                          int32_t* rank2_dev, void* ws, size_t ws_bytes, void* stream) {
-  if (nseg < 0 || m < 1 || m > 1024 || ld < m) return GINI_EINVAL;
+  if (nseg < 0 || m < 1 || m > (int64_t)LONG_CHUNK * LONG_MAX_CHUNKS || ld < m) return GINI_EINVAL;
   if (nseg == 0) return GINI_OK;  // nothing to rank; pointers may be null
   if (!v_dev || !rank2_dev || !ws) return GINI_EINVAL;
   if (ws_misaligned(ws)) return GINI_EINVAL;
   if (ws_bytes < gini_workspace_size(GINI_OP_RANK, nseg, m, 0, 0)) return GINI_ENOMEM;
   if (nseg > ((int64_t)1 << 34)) return GINI_EINVAL;  // grid size limit
+  if (m > LONG_CHUNK && nseg > ((int64_t)1 << 31)) return GINI_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   unsigned* err = reinterpret_cast<unsigned*>(ws);
   const int mi = (int)m;
@@ -95,7 +140,18 @@ extern "C" int gini_rank(const float* v_dev, int64_t nseg, int64_t m, int64_t ld
   else if (m <= 128) e = launch_rank<16, 8>(v_dev, nseg, mi, ld, rank2_dev, err, s);
   else if (m <= 256) e = launch_rank<16, 16>(v_dev, nseg, mi, ld, rank2_dev, err, s);
   else if (m <= 512) e = launch_rank<16, 32>(v_dev, nseg, mi, ld, rank2_dev, err, s);
-  else e = launch_rank<32, 32>(v_dev, nseg, mi, ld, rank2_dev, err, s);
+  else if (m <= LONG_CHUNK) e = launch_rank<32, 32>(v_dev, nseg, mi, ld, rank2_dev, err, s);
+  else {
+    const int nchunk = (mi + LONG_CHUNK - 1) / LONG_CHUNK;
+    const size_t smem = sizeof(unsigned long long) * RANK_LONG_WARPS * nchunk * LONG_CHUNK_SLOTS;
+    e = cudaFuncSetAttribute(k_rank_long, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) {
+      gini_count_launch(1);
+      k_rank_long<<<(unsigned)((nseg + RANK_LONG_WARPS - 1) / RANK_LONG_WARPS),
+                    RANK_LONG_WARPS * 32, smem, s>>>(v_dev, nseg, mi, ld, nchunk, rank2_dev, err);
+      e = cudaGetLastError();
+    }
+  }
   if (e != cudaSuccess) { gini_set_cuda_error(e); return GINI_ECUDA; }
   return GINI_OK;
 }

@@ -298,3 +298,49 @@ __device__ __forceinline__ int seg_first_run_start(const T (&v)[E], int ls, KeyE
 }
 
 }  // namespace gini
+
+namespace gini {
+
+// ---------------------------------------------------------------------------
+// Long segments (m > 1024): a warp sorts the segment in chunks of 1024 slots
+// (32 registers x 32 lanes, the 64-bit network above) into shared memory, and
+// each element's rank comes from binary searches in every sorted chunk.
+
+constexpr int LONG_CHUNK = 1024;
+constexpr int LONG_MAX_CHUNKS = 8;  // m <= 8192
+
+// Shared-memory index of sorted position pos: one word of padding per 32
+// keys, so the 32 lanes' stores of one register fall into 16 banks.
+__device__ __forceinline__ int long_slot(int pos) { return pos + (pos >> 5); }
+constexpr int LONG_CHUNK_SLOTS = LONG_CHUNK + LONG_CHUNK / 32;
+
+// Sorts this warp's chunk of keys (kv[t] = key of chunk position t * 32 +
+// lane, ~0 for padding) and stores it ascending at dst[long_slot(pos)].
+__device__ __forceinline__ void long_sort_chunk(unsigned long long (&kv)[32], int lane,
+                                                unsigned long long* dst) {
+  seg_bitonic_sort<32, 32>(kv, lane);
+#pragma unroll
+  for (int t = 0; t < 32; ++t) dst[long_slot(lane * 32 + t)] = kv[t];
+}
+
+// Number of keys below k and equal to k in sorted a[0 .. len) (indices
+// through long_slot).
+__device__ __forceinline__ void long_count(const unsigned long long* a, int len,
+                                           unsigned long long k, int& lt, int& eq) {
+  int lo = 0, hi = len;  // first index with a >= k
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (a[long_slot(mid)] < k) lo = mid + 1;
+    else hi = mid;
+  }
+  int lo2 = lo, hi2 = len;  // first index with a > k
+  while (lo2 < hi2) {
+    const int mid = (lo2 + hi2) >> 1;
+    if (a[long_slot(mid)] <= k) lo2 = mid + 1;
+    else hi2 = mid;
+  }
+  lt += lo;
+  eq += lo2 - lo;
+}
+
+}  // namespace gini

@@ -75,13 +75,13 @@ def test_host_side_validation(L):
     EINVAL, EDEG, ENOMEM = _lib.GINI_EINVAL, _lib.GINI_EDEGENERATE, _lib.GINI_ENOMEM
     # gini_rank: m out of range, ld < m, missing pointers
     assert L.gini_rank(fake, 4, 0, 4, fake, ws, 1 << 20, None) == EINVAL
-    assert L.gini_rank(fake, 4, 1025, 2048, fake, ws, 1 << 20, None) == EINVAL
+    assert L.gini_rank(fake, 4, 8193, 9000, fake, ws, 1 << 20, None) == EINVAL
     assert L.gini_rank(fake, 4, 8, 4, fake, ws, 1 << 20, None) == EINVAL
     assert L.gini_rank(None, 4, 8, 8, fake, ws, 1 << 20, None) == EINVAL
     # gini_dist: nu <= 1, n < 2, p > 1024, FULL needs F32, small workspace
     assert L.gini_dist(fake, 10, 5, 5, bad_nu, 1, 0, 0, fake, 10, 100, None, None, ws, 1 << 20, None) == EINVAL
     assert L.gini_dist(fake, 1, 5, 5, nu, 1, 0, 0, fake, 10, 100, None, None, ws, 1 << 20, None) == EINVAL
-    assert L.gini_dist(fake, 10, 1025, 1025, nu, 1, 0, 0, fake, 10, 100, None, None, ws, 1 << 20, None) == EINVAL
+    assert L.gini_dist(fake, 10, 8193, 8193, nu, 1, 0, 0, fake, 10, 100, None, None, ws, 1 << 20, None) == EINVAL
     assert L.gini_dist(fake, 10, 5, 5, nu, 1, 0, 1, fake, 10, 100, None, None, ws, 1 << 20, None) == EINVAL
     assert L.gini_dist(fake, 10, 5, 5, nu, 1, 1, 3, fake, 10, 100, None, None, ws, 1 << 20, None) == EINVAL
     assert L.gini_dist(fake, 10, 5, 5, nu, 1, 0, 0, fake, 10, 100, None, None, ws, 8, None) == ENOMEM

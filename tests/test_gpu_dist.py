@@ -309,3 +309,27 @@ def test_delta_fp8_output_direct(G, strips):
     # the Python binding's FP8 path and a stress evaluation on it
     m8, _ = G.gini_dist(Xd, nus, layout="tiled", dtype="fp8")
     assert torch.equal(m8[0].data, out[:plane]) and torch.equal(m8[0].col_scale, scale[:n])
+
+
+@pytest.mark.parametrize("p", [1025, 2048, 3072])
+@pytest.mark.parametrize("nus", [[2.0], [1.5, 2.0, 3.0]])
+def test_delta_vectors_longer_than_a_warp(G, p, nus):
+    # 1024 < p: the pair's differences are sorted in 1024-slot chunks and
+    # ranked by search; exact (hi, lo) order for every nu, ties included.
+    n = 19
+    rng = np.random.default_rng(5400 + p)
+    X = rng.standard_normal((n, p)).astype(np.float32)
+    X[:, ::7] = np.round(X[:, ::7])  # ties within and across chunks
+    X[5] = np.round(X[5] * 8) / 8     # multiples of 1/8: adding 1/4 is exact,
+    X[3] = X[5] + np.float32(0.25)   # so this pair's differences all tie
+    ref, sref = orc.delta(X, nus)
+    got, sd2 = _gpu_full(G, X, nus)
+    for q in range(len(nus)):
+        _check_full(got[q], ref[q])
+        assert sd2[q] == pytest.approx(sref[q], rel=1e-5)
+    assert np.all(got[0][3, 5] == 0.0)
+    mats, _ = G.gini_dist(torch.from_numpy(X).cuda(), nus, layout="tiled", dtype="bf16x2")
+    iu = np.triu_indices(n, 1)
+    for q in range(len(nus)):
+        t = untile(mats[q].data.float().cpu().numpy(), n, 2)
+        assert rel_err(t[iu], ref[q][iu], 1e-6 * np.abs(ref[q]).max()) <= ENTRY_TOL["bf16x2"]

@@ -9,7 +9,8 @@ from paper_2605_25124_gb300 import workloads as wl
 pytestmark = pytest.mark.gpu
 
 SIZES = [1, 2, 3, 4, 5, 7, 8, 9, 15, 16, 17, 31, 32, 33, 63, 64, 65, 100, 127, 128, 129,
-         255, 256, 257, 500, 511, 512, 513, 784, 1000, 1023, 1024]
+         255, 256, 257, 500, 511, 512, 513, 784, 1000, 1023, 1024,
+         1025, 2048, 3072, 4100, 8192]  # above 1024: chunked sort + search
 
 
 def _ref(v):
