@@ -480,14 +480,34 @@ def _batched_summary(G, dev, stream, steps=2):
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1))
     G.workspace(dev).check()
+    fin32 = out["final"].clone()
+    # the same batch with the Delta pool in BF16 (half the memory)
+    ob = G.gini_fit_batched(Xs, nus, R, T, Y0, check_errors=False, delta_dtype="bf16")
+    torch.cuda.synchronize()
+    tb = []
+    for _ in range(steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ob = G.gini_fit_batched(Xs, nus, R, T, Y0, check_errors=False, delta_dtype="bf16")
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tb.append(e0.elapsed_time(e1))
+    G.workspace(dev).check()
+    rel = ((ob["final"] - fin32).abs() / fin32).cpu().numpy()
     nfits = len(ns) * len(nus) * R
     pairs = sum(n * (n - 1) // 2 for n in ns) * len(nus)
-    ms = statistics.mean(times)
+    ms, msb = statistics.mean(times), statistics.mean(tb)
     return {"workload": name, "fits": nfits, "iters": T, "ms_per_batch": round(ms, 3),
             "fit_iters_per_s": round(nfits * T / (ms / 1e3), 1),
             "delta_pairs_all_nu": pairs,
             "achieved_delta_gbs": round(pairs * 4 * T / (ms / 1e3) / 1e9, 1),
             "tuned_rows_x100_plus_ctas_per_sm": out["tuned"],
+            "bf16_pool": {"ms_per_batch": round(msb, 3),
+                          "fit_iters_per_s": round(nfits * T / (msb / 1e3), 1),
+                          "pool_bytes_vs_f32": 0.5,
+                          "final_stress_rel_diff_vs_f32_pool_median": float(np.median(rel)),
+                          "final_stress_rel_diff_vs_f32_pool_max": float(rel.max()),
+                          "tuned_rows_x100_plus_ctas_per_sm": ob["tuned"]},
             "note": "each batch includes its 64 Delta builds (8 nu from one sort per pair)"}
 
 

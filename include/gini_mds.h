@@ -313,9 +313,20 @@ typedef struct {
   int64_t ldx;         /* >= p */
 } gini_problem;
 
-/* Bytes of workspace gini_fit_batched needs for these problems. */
+/* Options of gini_fit_batched (NULL: all zero). */
+typedef struct {
+  int deterministic;  /* 1: per (tile, restart) partials summed in a fixed order instead of
+                         atomics, so results repeat bit for bit (also on when the thread's mode
+                         is, gini_set_deterministic); needs the larger workspace below */
+  int delta_dtype;    /* storage of the Delta pool: GINI_F32 (0) or GINI_BF16 (half the
+                         memory; the iterations read bf16 values) */
+  int tile_rows;      /* 0: the autotuner chooses; else 8 or 16 rows of a tile per warp ... */
+  int ctas_per_sm;    /* ... and 1..3 CTAs per SM */
+} gini_batch_opts;
+
+/* Bytes of workspace gini_fit_batched needs for these problems and options. */
 size_t gini_batch_workspace_size(const gini_problem* probs, int nprob, int n_nu, int restarts,
-                                 int iters, int deterministic);
+                                 int iters, const gini_batch_opts* opts);
 
 /* Many k = 2 fits at once: every problem x every nu of the grid x `restarts`
  * starting points (the loops of Algorithm 1 over nu and starts).  For each
@@ -337,17 +348,15 @@ size_t gini_batch_workspace_size(const gini_problem* probs, int nprob, int n_nu,
  *   history_dev  (iters + 1) x nfits doubles out (S after t iterations), or NULL;
  *                fits are ordered (problem, nu, restart)
  *   final_stress_dev  nfits doubles out, S(Y_T)
- *   tuned_config out (host), or NULL: 100 x rows-per-warp + CTAs per SM chosen
- *   deterministic  1: per (tile, restart) partials summed in a fixed order
- *                instead of atomics, so results repeat bit for bit (also on when
- *                the thread's mode is, gini_set_deterministic); it needs the
- *                workspace gini_batch_workspace_size(..., 1) reports (about
- *                1 KB more per tile and restart)
+ *   tuned_config out (host), or NULL: 100 x rows-per-warp + CTAs per SM used
+ *   opts         gini_batch_opts, or NULL for the defaults (atomics, FP32 pool,
+ *                autotuned shape); the workspace must be sized with the same
+ *                options
  * Non-finite data are reported by gini_check(ws, stream). */
 int gini_fit_batched(const gini_problem* probs, int nprob, const double* nu_host, int n_nu,
                      int restarts, int iters, double eta0, const float* Y0_dev, float* Y_dev,
                      double* history_dev, double* final_stress_dev, int* tuned_config,
-                     int deterministic, void* ws, size_t ws_bytes, void* stream);
+                     const gini_batch_opts* opts, void* ws, size_t ws_bytes, void* stream);
 
 /* Bytes of workspace gini_nu_search needs (0 on invalid folds or sizes). */
 size_t gini_nu_search_workspace_size(int64_t n, int64_t p, const int32_t* fold_host, int K,

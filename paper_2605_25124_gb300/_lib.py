@@ -28,6 +28,12 @@ class Problem(_c.Structure):
     _fields_ = [("X_dev", _vp), ("n", _i64), ("p", _i64), ("ldx", _i64)]
 
 
+class BatchOpts(_c.Structure):
+    """Mirror of gini_batch_opts in include/gini_mds.h."""
+    _fields_ = [("deterministic", _c.c_int), ("delta_dtype", _c.c_int), ("tile_rows", _c.c_int),
+                ("ctas_per_sm", _c.c_int)]
+
+
 class FitArgs(_c.Structure):
     """Mirror of gini_fit_args in include/gini_mds.h."""
     _fields_ = [
@@ -87,10 +93,11 @@ SIGNATURES = {
                                             _c.c_int, _i64, _vp, _c.c_double, _vp, _vp, _vp]),
     "gini_default_step": (_c.c_double, [_i64, _c.c_int, _c.c_double, _c.c_double, _c.c_double]),
     "gini_batch_workspace_size": (_c.c_size_t, [_c.POINTER(Problem), _c.c_int, _c.c_int,
-                                                _c.c_int, _c.c_int, _c.c_int]),
+                                                _c.c_int, _c.c_int, _c.POINTER(BatchOpts)]),
     "gini_fit_batched": (_c.c_int, [_c.POINTER(Problem), _c.c_int, _c.POINTER(_c.c_double),
                                     _c.c_int, _c.c_int, _c.c_int, _c.c_double, _vp, _vp, _vp,
-                                    _vp, _c.POINTER(_c.c_int), _c.c_int, _vp, _c.c_size_t, _vp]),
+                                    _vp, _c.POINTER(_c.c_int), _c.POINTER(BatchOpts), _vp,
+                                    _c.c_size_t, _vp]),
     "gini_set_deterministic": (None, [_c.c_int]),
     "gini_get_deterministic": (_c.c_int, []),
 }

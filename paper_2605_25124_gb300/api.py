@@ -258,8 +258,12 @@ def gini_mds_fit(Y0: torch.Tensor, nu: float, D: Dissimilarity, eta: float, iter
 
 def gini_fit_batched(Xs, nus, restarts: int, iters: int, Y0: torch.Tensor, eta0: float = 1.0,
                      history: bool = False, ws: Optional[Workspace] = None,
-                     check_errors: bool = True, deterministic: bool = False):
+                     check_errors: bool = True, deterministic: bool = False,
+                     delta_dtype: str = "f32", tile=None):
     """Batched k = 2 fits of every problem x nu x restart.
+
+    delta_dtype: storage of the Delta pool, "f32" or "bf16".  tile: None (the
+    autotuner chooses) or (rows per warp 8 | 16, CTAs per SM 1..3).
 
     Xs: list of (n_q, p_q) float32 CUDA tensors.  Y0: flat float32 tensor,
     problem-major, restarts x n_q x 2 per problem.  Returns a dict with
@@ -283,15 +287,20 @@ def gini_fit_batched(Xs, nus, restarts: int, iters: int, Y0: torch.Tensor, eta0:
     nfits = nprob * n_nu * restarts
     final = torch.empty(nfits, dtype=torch.float64, device=dev)
     hist = torch.empty((iters + 1) * nfits, dtype=torch.float64, device=dev) if history else None
-    det = int(bool(deterministic) or is_deterministic())
-    nbytes = int(lib().gini_batch_workspace_size(probs, nprob, n_nu, restarts, iters, det))
+    opts = _lib.BatchOpts(deterministic=int(bool(deterministic) or is_deterministic()),
+                          delta_dtype=DTYPES[delta_dtype],
+                          tile_rows=int(tile[0]) if tile else 0,
+                          ctas_per_sm=int(tile[1]) if tile else 0)
+    nbytes = int(lib().gini_batch_workspace_size(probs, nprob, n_nu, restarts, iters,
+                                                 ctypes.byref(opts)))
     ws = ws or workspace(dev)
     buf = ws.ensure(nbytes)
     nu_arr = (ctypes.c_double * n_nu)(*nus)
     tuned = ctypes.c_int(0)
     st = lib().gini_fit_batched(probs, nprob, nu_arr, n_nu, restarts, iters, float(eta0),
                                 _ptr(Y0.contiguous()), _ptr(Y), _ptr(hist), _ptr(final),
-                                ctypes.byref(tuned), det, _ptr(buf), buf.numel(), _stream())
+                                ctypes.byref(tuned), ctypes.byref(opts), _ptr(buf), buf.numel(),
+                                _stream())
     check(st, "gini_fit_batched")
     if check_errors:
         ws.check()

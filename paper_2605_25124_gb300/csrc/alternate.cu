@@ -121,6 +121,7 @@ extern "C" int gini_alternating_nu(const float* X_dev, int64_t n, int64_t p, int
                                    int iters, double eta0, int metric, int loss, float* Y_dev,
                                    double* nu_path_host, double* ks_host, void* ws,
                                    size_t ws_bytes, void* stream) {
+  NvtxRange nvtx_range("gini_alternating_nu");
   if (!X_dev || !nu_host || !Y_dev || !nu_path_host || !ks_host || !ws) return GINI_EINVAL;
   if (ws_misaligned(ws)) return GINI_EINVAL;
   if (n < 2 || p < 1 || p > 8192 || ldx < p || k < 2 || k > 8 || n_nu < 1 || n_nu > 64 ||

@@ -48,7 +48,7 @@ struct BatchParams {
   int nseg;
   int restarts;
   int64_t total_tiles;
-  const float* delta;  // tiled FP32 pool
+  const void* delta;   // tiled pool of every segment's Delta (FP32 or BF16)
   float2* P;           // point pairs (hi, lo of y0 - y1)
   float* h;            // gradient accumulators
   double* acc;         // stress accumulators of the current pass: one per fit
@@ -107,7 +107,7 @@ __device__ __forceinline__ int row_of_lane(int lane) {
 // Persistent batched iteration.  ROWS rows of a tile per warp, TILE / ROWS
 // warps per CTA; lane l takes columns 4l .. 4l+3.  GRAD = false is the final
 // stress-only pass.
-template <int ROWS, bool GRAD>
+template <int ROWS, bool GRAD, int DT>
 __global__ void __launch_bounds__(TILE / ROWS * 32) k_batch_iter(const BatchParams B) {
   constexpr int WARPS = TILE / ROWS;
   constexpr int NT = WARPS * 32;
@@ -142,12 +142,22 @@ __global__ void __launch_bounds__(TILE / ROWS * 32) k_batch_iter(const BatchPara
     const int64_t n = sg.n;
     const int64_t i0 = (int64_t)I * TILE, j0 = (int64_t)J * TILE;
     const int64_t t_local = g - sg.tile_begin;
-    const float* tile = B.delta + sg.delta_off + t_local * (int64_t)(TILE * TILE);
-    // this thread's ROWS x 4 dissimilarities, kept in registers for all restarts
+    const int64_t tile_off = sg.delta_off + t_local * (int64_t)(TILE * TILE);
+    // this thread's ROWS x 4 dissimilarities, kept in registers (as floats)
+    // for all restarts
     float4 d[ROWS];
 #pragma unroll
-    for (int q = 0; q < ROWS; ++q)
-      d[q] = __ldcs(reinterpret_cast<const float4*>(tile + (warp * ROWS + q) * TILE + 4 * lane));
+    for (int q = 0; q < ROWS; ++q) {
+      const int64_t off = tile_off + (warp * ROWS + q) * TILE + 4 * lane;
+      if (DT == GINI_F32) {
+        d[q] = __ldcs(reinterpret_cast<const float4*>(reinterpret_cast<const float*>(B.delta) + off));
+      } else {  // GINI_BF16: four bf16 values in 8 bytes
+        const uint2 h = __ldcs(reinterpret_cast<const uint2*>(
+            reinterpret_cast<const uint16_t*>(B.delta) + off));
+        d[q] = make_float4(bf16_bits_to_float(h.x & 0xffffu), __uint_as_float(h.x & 0xffff0000u),
+                           bf16_bits_to_float(h.y & 0xffffu), __uint_as_float(h.y & 0xffff0000u));
+      }
+    }
     __syncthreads();  // previous tile's shared data fully consumed
     for (int e = threadIdx.x; e < 2 * R * TILE; e += NT) {
       const int side = e / (R * TILE), rr = (e / TILE) % R, l = e % TILE;
@@ -373,7 +383,7 @@ static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct BatchWs {
   unsigned* err;
-  float* delta;
+  void* delta;
   double* sd2;
   BatchSeg* segs;
   int64_t* pt_prefix;
@@ -388,7 +398,7 @@ struct BatchWs {
 };
 
 static BatchWs batch_layout(const BatchPlan& pl, int nprob, int n_nu, int iters, bool det,
-                            char* base) {
+                            int dtype, char* base) {
   BatchWs w{};
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -400,7 +410,7 @@ static BatchWs batch_layout(const BatchPlan& pl, int nprob, int n_nu, int iters,
   // first, so its error word is the batch's error word too.
   w.wtab = (float*)take(gini_workspace_size(GINI_OP_DIST, 2, pl.max_p, 0, 0));
   w.err = (unsigned*)w.wtab;
-  w.delta = (float*)take(sizeof(float) * (size_t)pl.delta_elems);
+  w.delta = take((dtype == GINI_BF16 ? 2 : 4) * (size_t)pl.delta_elems);
   w.sd2 = (double*)take(sizeof(double) * (size_t)nprob * n_nu);
   w.segs = (BatchSeg*)take(sizeof(BatchSeg) * pl.segs.size());
   w.pt_prefix = (int64_t*)take(sizeof(int64_t) * pl.segs.size());
@@ -465,7 +475,20 @@ static BatchPlan make_plan(const gini_problem* probs, int nprob, const double* n
 struct TuneChoice {
   int rows = 16;     // rows of a tile per warp (16 -> 8 warps, 8 -> 16 warps per CTA)
   int per_sm = 2;    // CTAs per SM
+  int dtype = GINI_F32;  // storage of the Delta pool
 };
+
+template <int DT>
+static void launch_iter_dt(const TuneChoice& tc, bool grad, unsigned grid, const BatchParams& P,
+                           cudaStream_t s) {
+  if (tc.rows == 16) {
+    if (grad) k_batch_iter<16, true, DT><<<grid, 8 * 32, 0, s>>>(P);
+    else k_batch_iter<16, false, DT><<<grid, 8 * 32, 0, s>>>(P);
+  } else {
+    if (grad) k_batch_iter<8, true, DT><<<grid, 16 * 32, 0, s>>>(P);
+    else k_batch_iter<8, false, DT><<<grid, 16 * 32, 0, s>>>(P);
+  }
+}
 
 static std::mutex g_tune_mu;
 static std::map<std::string, TuneChoice> g_tune_cache;
@@ -481,31 +504,28 @@ static void launch_iter(const TuneChoice& tc, bool grad, const BatchParams& P, c
   const int64_t cap = (int64_t)sms_of_current_device() * tc.per_sm;
   const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(P.total_tiles, cap));
   gini_count_launch(1);
-  if (tc.rows == 16) {
-    if (grad) k_batch_iter<16, true><<<grid, 8 * 32, 0, s>>>(P);
-    else k_batch_iter<16, false><<<grid, 8 * 32, 0, s>>>(P);
-  } else {
-    if (grad) k_batch_iter<8, true><<<grid, 16 * 32, 0, s>>>(P);
-    else k_batch_iter<8, false><<<grid, 16 * 32, 0, s>>>(P);
-  }
+  if (tc.dtype == GINI_BF16) launch_iter_dt<GINI_BF16>(tc, grad, grid, P, s);
+  else launch_iter_dt<GINI_F32>(tc, grad, grid, P, s);
 }
 
-static std::string tune_key(const BatchPlan& pl, int R) {
-  // same tile counts and restarts -> same choice
+static std::string tune_key(const BatchPlan& pl, int R, int dtype) {
+  // same tile counts, restarts and storage -> same choice
   return std::to_string(pl.total_tiles) + "/" + std::to_string(pl.segs.size()) + "/" +
-         std::to_string(R);
+         std::to_string(R) + "/" + std::to_string(dtype);
 }
 
 // Times every candidate on one gradient pass of the real batch (the
 // accumulators it disturbs are reset by the graph before the fit proper).
-static TuneChoice autotune(const BatchPlan& pl, int R, const BatchParams& P, cudaStream_t s) {
-  const std::string key = tune_key(pl, R);
+static TuneChoice autotune(const BatchPlan& pl, int R, int dtype, const BatchParams& P,
+                           cudaStream_t s) {
+  const std::string key = tune_key(pl, R, dtype);
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     auto it = g_tune_cache.find(key);
     if (it != g_tune_cache.end()) return it->second;
   }
-  const TuneChoice cands[] = {{16, 1}, {16, 2}, {16, 3}, {8, 1}, {8, 2}};
+  const TuneChoice cands[] = {{16, 1, dtype}, {16, 2, dtype}, {16, 3, dtype}, {8, 1, dtype},
+                              {8, 2, dtype}};
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -548,24 +568,39 @@ using namespace gini;
 extern "C" void gini_set_cuda_error(cudaError_t e);
 extern "C" int gini_get_deterministic(void);
 
+static bool batch_det(const gini_batch_opts* o) {
+  return (o && o->deterministic) || gini_get_deterministic();
+}
+
+static int batch_dtype(const gini_batch_opts* o) { return o ? o->delta_dtype : GINI_F32; }
+
 extern "C" size_t gini_batch_workspace_size(const gini_problem* probs, int nprob, int n_nu,
-                                            int restarts, int iters, int deterministic) {
+                                            int restarts, int iters,
+                                            const gini_batch_opts* opts) {
   if (!probs || nprob < 1 || n_nu < 1 || restarts < 1 || iters < 0) return 0;
   std::vector<double> nu(n_nu, 2.0);
   BatchPlan pl = make_plan(probs, nprob, nu.data(), n_nu, restarts, 1.0);
-  return batch_layout(pl, nprob, n_nu, iters, deterministic != 0, nullptr).total;
+  return batch_layout(pl, nprob, n_nu, iters, batch_det(opts), batch_dtype(opts), nullptr).total;
 }
 
 extern "C" int gini_fit_batched(const gini_problem* probs, int nprob, const double* nu_host,
                                 int n_nu, int restarts, int iters, double eta0,
                                 const float* Y0_dev, float* Y_dev, double* history_dev,
-                                double* final_stress_dev, int* tuned_rows, int deterministic,
-                                void* ws, size_t ws_bytes, void* stream) {
+                                double* final_stress_dev, int* tuned_rows,
+                                const gini_batch_opts* opts, void* ws, size_t ws_bytes,
+                                void* stream) {
+  NvtxRange nvtx_range("gini_fit_batched");
   if (!probs || !nu_host || !Y0_dev || !Y_dev || !ws) return GINI_EINVAL;
   if (ws_misaligned(ws)) return GINI_EINVAL;
   if (nprob < 1 || n_nu < 1 || n_nu > 8 || restarts < 1 || restarts > BATCH_RMAX || iters < 0)
     return GINI_EINVAL;
   if (!(eta0 > 0.0) || !isfinite(eta0)) return GINI_EINVAL;
+  const int dtype = batch_dtype(opts);
+  if (dtype != GINI_F32 && dtype != GINI_BF16) return GINI_EINVAL;
+  if (opts && opts->tile_rows &&
+      ((opts->tile_rows != 8 && opts->tile_rows != 16) || opts->ctas_per_sm < 1 ||
+       opts->ctas_per_sm > 3))
+    return GINI_EINVAL;
   for (int v = 0; v < n_nu; ++v)
     if (!(nu_host[v] > 1.0) || !isfinite(nu_host[v])) return GINI_EINVAL;
   for (int q = 0; q < nprob; ++q) {
@@ -575,8 +610,8 @@ extern "C" int gini_fit_batched(const gini_problem* probs, int nprob, const doub
   }
   BatchPlan pl = make_plan(probs, nprob, nu_host, n_nu, restarts, eta0);
   if (pl.nfits > (1 << 30)) return GINI_EINVAL;
-  const bool det = deterministic || gini_get_deterministic();
-  BatchWs w = batch_layout(pl, nprob, n_nu, iters, det, reinterpret_cast<char*>(ws));
+  const bool det = batch_det(opts);
+  BatchWs w = batch_layout(pl, nprob, n_nu, iters, det, dtype, reinterpret_cast<char*>(ws));
   if (ws_bytes < w.total) return GINI_ENOMEM;
   cudaStream_t s = (cudaStream_t)stream;
 
@@ -586,8 +621,10 @@ extern "C" int gini_fit_batched(const gini_problem* probs, int nprob, const doub
     const BatchSeg& s0 = pl.segs[(size_t)q * n_nu];
     const int64_t plane = gini_tiled_elems(probs[q].n);
     const int st = gini_dist(probs[q].X_dev, probs[q].n, probs[q].p, probs[q].ldx, nu_host, n_nu,
-                             GINI_LAYOUT_TILED, GINI_F32, w.delta + s0.delta_off, 0, plane,
-                             nullptr, w.sd2 + (size_t)q * n_nu, w.wtab,
+                             GINI_LAYOUT_TILED, dtype,
+                             reinterpret_cast<char*>(w.delta) +
+                                 (size_t)s0.delta_off * (dtype == GINI_BF16 ? 2 : 4),
+                             0, plane, nullptr, w.sd2 + (size_t)q * n_nu, w.wtab,
                              gini_workspace_size(GINI_OP_DIST, 2, pl.max_p, 0, 0), stream);
     if (st != GINI_OK) return st;
   }
@@ -630,14 +667,16 @@ extern "C" int gini_fit_batched(const gini_problem* probs, int nprob, const doub
   // 3. Autotune on the real batch (first call for this shape only).
   init();
   P.acc = w.acc;
-  TuneChoice tc = autotune(pl, restarts, P, s);
+  TuneChoice tc;
+  if (opts && opts->tile_rows) tc = TuneChoice{opts->tile_rows, opts->ctas_per_sm, dtype};
+  else tc = autotune(pl, restarts, dtype, P, s);
   if (tuned_rows) *tuned_rows = tc.rows * 100 + tc.per_sm;
 
   // 4. The fit as one graph: reset, T x (iteration + update), final pass, finalize.
   char keybuf[512];
-  snprintf(keybuf, sizeof(keybuf), "%p/%p/%p/%p/%p/%d/%d/%d/%lld/%d/%d/%d", ws,
+  snprintf(keybuf, sizeof(keybuf), "%p/%p/%p/%p/%p/%d/%d/%d/%lld/%d/%d/%d/%d", ws,
            (const void*)Y0_dev, (void*)Y_dev, (void*)history_dev, (void*)final_stress_dev, iters,
-           restarts, nprob, (long long)pl.total_tiles, tc.rows, tc.per_sm, det ? 1 : 0);
+           restarts, nprob, (long long)pl.total_tiles, tc.rows, tc.per_sm, det ? 1 : 0, dtype);
   std::string key(keybuf);
   for (int q = 0; q < nprob; ++q) key += "/" + std::to_string((long long)probs[q].n);
   for (int v = 0; v < n_nu; ++v) key += "/" + std::to_string(nu_host[v]);

@@ -155,6 +155,7 @@ __global__ void k_pack(const float* __restrict__ D, int64_t n, int64_t ldd, int6
 
 extern "C" int gini_pack(const float* delta_full_dev, int64_t n, int64_t ldd, int dtype,
                          void* packed_dev, float* col_scale_dev, void* stream) {
+  NvtxRange nvtx_range("gini_pack");
   if (!delta_full_dev || !packed_dev || n < 2 || ldd < n || n > ((int64_t)1 << 31))
     return GINI_EINVAL;
   if (dtype < GINI_F32 || dtype > GINI_FP8E4M3) return GINI_EINVAL;

@@ -355,6 +355,7 @@ extern "C" int gini_classical_mds(const void* delta_dev, int64_t n, int layout, 
                                   int64_t ldd, const float* col_scale_dev, int k, int iters,
                                   uint64_t seed, float* Y_dev, double* eigvals_dev, void* ws,
                                   size_t ws_bytes, void* stream) {
+  NvtxRange nvtx_range("gini_classical_mds");
   if (!delta_dev || !Y_dev || !eigvals_dev || !ws) return GINI_EINVAL;
   if (ws_misaligned(ws)) return GINI_EINVAL;
   if (n < 2 || n > ((int64_t)1 << 31) || k < 1 || k > CMDS_KMAX || k > n || iters < 1)

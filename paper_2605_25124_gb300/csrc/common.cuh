@@ -4,6 +4,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include "gini_mds.h"
@@ -87,5 +88,16 @@ __device__ __forceinline__ float bf16_bits_to_float(uint32_t h16) {
 // regions are 256-byte multiples from the start, so every region keeps the
 // alignment bulk copies and vector loads need.
 inline bool ws_misaligned(const void* ws) { return (reinterpret_cast<uintptr_t>(ws) & 255) != 0; }
+
+// NVTX range around an entry point's host work (the enqueueing of its
+// kernels), named after the entry point, so profilers can group the kernels
+// by call (ncu --nvtx --nvtx-include "gini_dist/").  Header-only NVTX 3: a
+// no-op unless a profiling tool is attached.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 }  // namespace gini

@@ -920,6 +920,7 @@ extern "C" int gini_dist(const float* X_dev, int64_t n, int64_t p, int64_t ldx,
                          const double* nu_host, int n_nu, int layout, int dtype, void* delta_dev,
                          int64_t ldd, int64_t nu_stride, float* col_scale_dev,
                          double* sum_delta2_dev, void* ws, size_t ws_bytes, void* stream) {
+  NvtxRange nvtx_range("gini_dist");
   if (!X_dev || !delta_dev || !nu_host || !ws) return GINI_EINVAL;
   if (ws_misaligned(ws)) return GINI_EINVAL;
   if (n < 2 || p < 1 || p > (int64_t)LONG_CHUNK * LONG_MAX_CHUNKS || ldx < p || n_nu < 1 ||

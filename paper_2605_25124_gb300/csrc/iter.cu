@@ -1376,6 +1376,7 @@ extern "C" int gini_stress_grad_ex(const float* Y_dev, int64_t n, int k, double 
                                    const float* col_scale_dev, int metric, int loss, double norm,
                                    double* stress_dev, float* grad_dev, void* ws, size_t ws_bytes,
                                    void* stream) {
+  NvtxRange nvtx_range("gini_stress_grad_ex");
   if (!Y_dev || !stress_dev || !ws) return GINI_EINVAL;
   if (ws_misaligned(ws)) return GINI_EINVAL;  // point pairs are bulk-copied from it
   if (metric != GINI_METRIC_GINI && metric != GINI_METRIC_EUCLID) return GINI_EINVAL;
@@ -1415,6 +1416,7 @@ extern "C" int gini_stress_grad(const float* Y_dev, int64_t n, int k, double nu,
 }
 
 extern "C" int gini_mds_fit(const gini_fit_args* a, void* ws, size_t ws_bytes, void* stream) {
+  NvtxRange nvtx_range("gini_mds_fit");
   if (!a || !ws || !a->Y_dev) return GINI_EINVAL;
   if (ws_misaligned(ws)) return GINI_EINVAL;
   int st = check_common(a->n, a->k, a->nu, a->delta_dev, a->layout, a->dtype, a->ldd,

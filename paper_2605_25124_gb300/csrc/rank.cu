@@ -121,6 +121,7 @@ extern "C" void gini_set_cuda_error(cudaError_t e);
 
 extern "C" int gini_rank(const float* v_dev, int64_t nseg, int64_t m, int64_t ld,
                          int32_t* rank2_dev, void* ws, size_t ws_bytes, void* stream) {
+  NvtxRange nvtx_range("gini_rank");
   if (nseg < 0 || m < 1 || m > (int64_t)LONG_CHUNK * LONG_MAX_CHUNKS || ld < m) return GINI_EINVAL;
   if (nseg == 0) return GINI_OK;  // nothing to rank; pointers may be null
   if (!v_dev || !rank2_dev || !ws) return GINI_EINVAL;

@@ -159,8 +159,7 @@ int plan_search(int64_t n, int64_t p, const int32_t* fold, int K, int n_nu, int 
   for (int q = 0; q < K; ++q)
     pl.probs[q] = gini_problem{nullptr, cnt[q + 1] - cnt[q], p, p};
   const int chunk = std::min(n_nu, SEARCH_CHUNK);
-  pl.batch_ws = gini_batch_workspace_size(pl.probs.data(), K, chunk, R, iters,
-                                          gini_get_deterministic());
+  pl.batch_ws = gini_batch_workspace_size(pl.probs.data(), K, chunk, R, iters, nullptr);
   if (!pl.batch_ws) return GINI_EINVAL;
   size_t off = al256(pl.batch_ws);
   pl.off_xg = off;   off += al256(sizeof(float) * (size_t)n * p);
@@ -189,6 +188,7 @@ extern "C" int gini_nu_search(const float* X_dev, int64_t n, int64_t p, int64_t 
                               int restarts, int iters, double eta0, const float* Y0_dev,
                               double* ks_dev, double* mean_ks_dev, int* best_dev, float* Y_dev,
                               void* ws, size_t ws_bytes, void* stream) {
+  NvtxRange nvtx_range("gini_nu_search");
   if (!X_dev || !nu_host || !Y0_dev || !ks_dev || !mean_ks_dev || !best_dev || !Y_dev || !ws)
     return GINI_EINVAL;
   if (ldx < p) return GINI_EINVAL;
@@ -219,8 +219,8 @@ extern "C" int gini_nu_search(const float* X_dev, int64_t n, int64_t p, int64_t 
   for (int v0 = 0; v0 < n_nu; v0 += SEARCH_CHUNK) {
     const int nc = std::min(SEARCH_CHUNK, n_nu - v0);
     st = gini_fit_batched(pl.probs.data(), K, nu_host + v0, nc, restarts, iters, eta0, Y0g,
-                          Ybuf + 2 * (size_t)restarts * n * v0, nullptr, fs, nullptr,
-                          gini_get_deterministic(), ws, pl.batch_ws, stream);
+                          Ybuf + 2 * (size_t)restarts * n * v0, nullptr, fs, nullptr, nullptr,
+                          ws, pl.batch_ws, stream);
     if (st != GINI_OK) return st;
     gini_count_launch(1);
     k_search_reduce<<<(unsigned)((K * nc + 127) / 128), 128, 0, s>>>(fs, K, nc, restarts, v0,

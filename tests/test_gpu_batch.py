@@ -6,6 +6,7 @@ import torch
 
 from oracle import gini_oracle as orc
 from paper_2605_25124_gb300 import workloads as wl
+from util import quantize
 
 pytestmark = pytest.mark.gpu
 
@@ -165,3 +166,34 @@ def test_batched_ten_steps_against_the_oracle(G):
           f"Y_10 max err / total move {worst_y:.3e}")
     assert worst_h <= 1e-5
     assert worst_y <= 1e-4
+
+
+@pytest.mark.parametrize("tile", [None, (8, 2)])
+def test_batched_bf16_pool_one_step_against_the_oracle(G, tile):
+    """The Delta pool in BF16 (half the memory): S(Y0) and the first step of
+    every fit against the oracle run on the same dissimilarities rounded to
+    bf16 on the host; also with the tile shape given instead of autotuned."""
+    ns, ps, nus, R = [150, 300, 77], [5, 12, 30], [1.5, 2.0, 3.0], 3
+    Xs = [wl.gaussian_outliers(n, p, seed=7300 + q) for q, (n, p) in enumerate(zip(ns, ps))]
+    Y0s = [wl.y_init(R * n, 2, seed=7310 + q) for q, n in enumerate(ns)]
+    Xd = [torch.from_numpy(X).cuda() for X in Xs]
+    Y0 = torch.from_numpy(np.concatenate([y.reshape(-1) for y in Y0s])).cuda()
+    out = G.gini_fit_batched(Xd, nus, R, 1, Y0, eta0=1.0, history=True, delta_dtype="bf16",
+                             tile=tile)
+    if tile:
+        assert out["tuned"] == tile[0] * 100 + tile[1]
+    Yb = out["Y"].cpu().numpy()
+    sl = _slices(ns, len(nus), R)
+    for q, n in enumerate(ns):
+        D, sd2 = orc.delta(Xs[q], nus)
+        for v, nu in enumerate(nus):
+            Dq = quantize(D[v], "bf16")  # the stored values; the step keeps the FP32 sum
+            eta = orc.default_step(n, 2, nu, sd2[v], 1.0)
+            for r in range(R):
+                y0 = Y0s[q][r * n:(r + 1) * n].astype(np.float64)
+                y1, h = orc.fit(Dq, nu, sd2[v], y0, eta, 1)
+                assert out["history"][0, q, v, r].item() == pytest.approx(h[0], rel=1e-5)
+                a, b = sl[q, v, r]
+                step = Yb[a:b].reshape(n, 2) - y0
+                assert np.max(np.abs(step - (y1 - y0))) <= (1e-5 * np.abs(y1 - y0).max()
+                                                           + 2e-7 * np.abs(y0).max()), (q, v, r)
