@@ -378,10 +378,17 @@ struct PipeCfg {
   static constexpr int urow_off = planes * plane_bytes;
   static constexpr int ucol_off = urow_off + CHUNK_ROWS * 8;
   static constexpr int stage_bytes = ucol_off + TILE * 8;
-  // 104 KB of stages + ~8.5 KB static per CTA keeps two CTAs on an SM
-  static constexpr int stages_raw = (104 * 1024) / stage_bytes;
+  // 104 KB of stages + ~8.5 KB static per CTA keeps two CTAs on an SM; the
+  // narrow forms (16-bit, 8-bit tiles) take ~54 KB so that three fit: there a
+  // chunk is half or a quarter of the FP32 bytes and the consumers' arithmetic
+  // per chunk is the same, so more warps, not more bytes in flight, is the gain
+  static constexpr int budget = (DT == GINI_BF16 || DT == GINI_FP8E4M3) ? 54 * 1024 : 104 * 1024;
+  static constexpr int stages_raw = budget / stage_bytes;
   static constexpr int stages = stages_raw > 8 ? 8 : stages_raw;
   static constexpr int smem = stages * stage_bytes;
+  // the narrow forms' three CTAs per SM, held to in registers too; 0 (no
+  // bound) for the wide forms, which their shared memory holds to two
+  static constexpr int min_ctas = budget < 64 * 1024 ? 3 : 0;
 };
 
 // Sums a[0..7] over the 32 lanes; lane l returns the total of entry
@@ -497,7 +504,8 @@ __device__ __forceinline__ void chunk_compute(const unsigned char* stage, int rb
 }
 
 template <int DT, bool GRAD>
-__global__ void __launch_bounds__(PIPE_THREADS) k_fused2(const IterParams Q, int64_t ntiles) {
+__global__ void __launch_bounds__(PIPE_THREADS, PipeCfg<DT>::min_ctas)
+k_fused2(const IterParams Q, int64_t ntiles) {
   using C = PipeCfg<DT>;
   constexpr int S = C::stages;
   extern __shared__ __align__(128) unsigned char s_stage[];
@@ -688,7 +696,7 @@ struct FusedKSmem {
 // GK: Gini metric and Kruskal loss only (the other branches compiled out, so the
 // unrolled body stays small enough for the instruction cache).
 template <int K, int DT, bool GRAD, bool GK>
-__global__ void __launch_bounds__(FUSED_THREADS) k_fusedk(const IterParams Q, int64_t ntiles) {
+__global__ void __launch_bounds__(FUSED_THREADS, 2) k_fusedk(const IterParams Q, int64_t ntiles) {
   constexpr int NP = K * (K - 1) / 2;
   extern __shared__ __align__(16) unsigned char s_raw[];
   FusedKSmem<K>& sm = *reinterpret_cast<FusedKSmem<K>*>(s_raw);
@@ -1243,7 +1251,9 @@ static void update(int k, float* Y, int64_t n, float2* P, float* h, float scale,
 template <int K, bool FWD>
 static void launch_full(const IterParams& Q, cudaStream_t s) {
   const int64_t blocks = (Q.n + 7) / 8;  // a warp per row, rows grid-strided
-  const unsigned g = (unsigned)(blocks < STRESS_SLOTS ? blocks : STRESS_SLOTS);
+  // only the forward pass writes a stress slot per CTA; the adjoint takes a
+  // warp per row over the whole grid
+  const unsigned g = (unsigned)(FWD && blocks > STRESS_SLOTS ? STRESS_SLOTS : blocks);
   gini_count_launch(1);
   k_full<K, FWD><<<g, 256, 0, s>>>(Q);
 }
