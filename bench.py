@@ -494,6 +494,9 @@ def _batched_summary(G, dev, stream, steps=2):
         tb.append(e0.elapsed_time(e1))
     G.workspace(dev).check()
     rel = ((ob["final"] - fin32).abs() / fin32).cpu().numpy()
+    # best of the restarts of each (problem, nu): what a user of the batch keeps
+    b32, b16 = fin32.amin(dim=2), ob["final"].amin(dim=2)
+    relb = ((b16 - b32).abs() / b32).cpu().numpy()
     nfits = len(ns) * len(nus) * R
     pairs = sum(n * (n - 1) // 2 for n in ns) * len(nus)
     ms, msb = statistics.mean(times), statistics.mean(tb)
@@ -506,7 +509,14 @@ def _batched_summary(G, dev, stream, steps=2):
                           "fit_iters_per_s": round(nfits * T / (msb / 1e3), 1),
                           "pool_bytes_vs_f32": 0.5,
                           "final_stress_rel_diff_vs_f32_pool_median": float(np.median(rel)),
+                          "final_stress_rel_diff_vs_f32_pool_p99": float(np.quantile(rel, 0.99)),
                           "final_stress_rel_diff_vs_f32_pool_max": float(rel.max()),
+                          "fits_rel_diff_above_1e-2": int((rel > 1e-2).sum()),
+                          "best_of_restarts_rel_diff_median": float(np.median(relb)),
+                          "best_of_restarts_rel_diff_max": float(relb.max()),
+                          "note": "fits above 1e-2 end in another local minimum (the BF16 "
+                                  "rounding of Delta, 2^-9 relative, moves their path); the "
+                                  "best restart of each (problem, nu) stays close",
                           "tuned_rows_x100_plus_ctas_per_sm": ob["tuned"]},
             "note": "each batch includes its 64 Delta builds (8 nu from one sort per pair)"}
 

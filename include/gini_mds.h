@@ -50,7 +50,8 @@ typedef enum {
   GINI_EDEGENERATE = 3, /* sum of squared dissimilarities is zero: stress undefined */
   GINI_ENOMEM = 4,      /* workspace smaller than gini_workspace_size */
   GINI_ECUDA = 5,       /* a CUDA runtime call failed (see gini_last_cuda_error) */
-  GINI_ETIMEOUT = 6     /* a bounded device-side wait expired (reported by gini_check) */
+  GINI_ETIMEOUT = 6,    /* a bounded device-side wait expired (reported by gini_check) */
+  GINI_EINDEX = 7       /* a device-side index check failed: debug builds only (gini_check) */
 } gini_status;
 
 /* Storage type of a dissimilarity matrix. */
@@ -148,8 +149,9 @@ void gini_set_deterministic(int on);
 int gini_get_deterministic(void);
 
 /* Synchronizes `stream`, then returns and clears the status the kernels
- * recorded in `ws` since the last gini_check (GINI_OK, GINI_ENONFINITE or
- * GINI_ETIMEOUT), or GINI_ECUDA if the stream reports an error. */
+ * recorded in `ws` since the last gini_check (GINI_OK, GINI_ENONFINITE,
+ * GINI_ETIMEOUT, or in debug builds GINI_EINDEX, which takes precedence), or
+ * GINI_ECUDA if the stream reports an error. */
 int gini_check(void* ws, void* stream);
 
 /* Segmented midranks (Definition 1 with midpoint ranks for ties,
@@ -485,6 +487,32 @@ int gini_distance_correlations(const float* X_dev, int64_t n, int64_t p, int64_t
  * usable.  It shows that an expired wait ends the kernel instead of hanging
  * the GPU.  ws: at least 256 bytes. */
 int gini_selftest_wait_timeout(uint64_t limit_ns, void* ws, size_t ws_bytes, void* stream);
+
+/* Debug builds.  The library compiled with -DGINI_DEBUG_CHECKS (the Python
+ * package's build(debug=True), loaded when GINI_DEBUG=1) checks the offsets its
+ * hot kernels compute against the extents the call's sizes define: rows of X
+ * and the weight tables in the Delta build, every stored Delta entry (FULL,
+ * TILED, the FP8 strips), the bulk-copied chunks and point pairs of the fused
+ * iteration, the Delta loads of the generic-k iteration, the plain form's rows,
+ * the deterministic partials, the batched pool, and the scatter of the ranks.
+ * A failed check skips the access it guards, sets the error bit that
+ * gini_check returns as GINI_EINDEX, and keeps the first failure's site (file
+ * id x 100000 + source line), index and bound, and the number of failures, in
+ * the workspace header.  Release builds compile the checks away.
+ *
+ * gini_debug_checks: 1 in a debug build, 0 otherwise.
+ * gini_debug_index_record: synchronises the device, reads the record of the
+ *   workspace ws and clears it (site 0: no failure since the last read).
+ * gini_selftest_index_check: (debug builds) one kernel that stores at
+ *   indices 8, 12, ..., 60 of a 64-float buffer in ws, checked against a bound
+ *   of 32: six stores pass, eight fail and are skipped (every index stays
+ *   inside the buffer, so a broken check could not write out of bounds);
+ *   gini_check then returns GINI_EINDEX.  ws: at least 512 bytes.  Release
+ *   builds return GINI_EINVAL and launch nothing. */
+int gini_debug_checks(void);
+int gini_debug_index_record(void* ws, uint32_t* site, int64_t* index, int64_t* bound,
+                            uint32_t* count);
+int gini_selftest_index_check(void* ws, size_t ws_bytes, void* stream);
 
 /* A step size for gini_mds_fit: eta0 times the inverse of a Gershgorin bound
  * on the Gauss-Newton curvature of S,

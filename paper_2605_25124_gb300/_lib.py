@@ -9,9 +9,13 @@ import ctypes
 import os
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libginimds.so")
+# GINI_DEBUG=1 loads the debug build (device-side index checks, see
+# gini_debug_checks in include/gini_mds.h), built by build.build(debug=True).
+DEBUG = os.environ.get("GINI_DEBUG") == "1"
+LIB_PATH = os.path.join(_HERE, "_build_debug" if DEBUG else "_build", "libginimds.so")
 
-GINI_OK, GINI_EINVAL, GINI_ENONFINITE, GINI_EDEGENERATE, GINI_ENOMEM, GINI_ECUDA, GINI_ETIMEOUT = range(7)
+(GINI_OK, GINI_EINVAL, GINI_ENONFINITE, GINI_EDEGENERATE, GINI_ENOMEM, GINI_ECUDA, GINI_ETIMEOUT,
+ GINI_EINDEX) = range(8)
 DTYPES = {"f32": 0, "bf16": 1, "bf16x2": 2, "fp8": 3}
 METRICS = {"gini": 0, "euclid": 1}
 LOSSES = {"kruskal": 0, "sammon": 1}
@@ -86,6 +90,10 @@ SIGNATURES = {
     "gini_distance_correlations": (_c.c_int, [_vp, _i64, _i64, _i64, _vp, _c.c_int, _c.c_int,
                                               _vp, _vp, _c.c_size_t, _vp]),
     "gini_selftest_wait_timeout": (_c.c_int, [_c.c_uint64, _vp, _c.c_size_t, _vp]),
+    "gini_debug_checks": (_c.c_int, []),
+    "gini_debug_index_record": (_c.c_int, [_vp, _c.POINTER(_c.c_uint32), _c.POINTER(_i64),
+                                           _c.POINTER(_i64), _c.POINTER(_c.c_uint32)]),
+    "gini_selftest_index_check": (_c.c_int, [_vp, _c.c_size_t, _vp]),
     "gini_cmds_workspace_size": (_c.c_size_t, [_i64, _c.c_int]),
     "gini_classical_mds": (_c.c_int, [_vp, _i64, _c.c_int, _c.c_int, _i64, _vp, _c.c_int,
                                       _c.c_int, _c.c_uint64, _vp, _vp, _vp, _c.c_size_t, _vp]),
@@ -119,9 +127,10 @@ def lib():
     global _lib
     if _lib is None:
         if not os.path.exists(LIB_PATH):
+            how = ("`python -c 'from paper_2605_25124_gb300 import build; build.build(debug=True)'`"
+                   if DEBUG else "`python -c 'import __graft_entry__ as g; g.build()'`")
             raise RuntimeError(
-                f"libginimds.so not found at {LIB_PATH}; build it with "
-                "`python -c 'import __graft_entry__ as g; g.build()'` (needs nvcc)")
+                f"libginimds.so not found at {LIB_PATH}; build it with {how} (needs nvcc)")
         L = ctypes.CDLL(LIB_PATH)
         for name, (res, args) in SIGNATURES.items():
             fn = getattr(L, name)

@@ -3,6 +3,10 @@
 Each .cu under csrc/ is compiled to an object in parallel, then linked into
 paper_2605_25124_gb300/_build/libginimds.so.  The CUDA runtime is linked
 statically, so the library needs only the driver at run time.
+
+build(debug=True) makes the debug library in _build_debug/ instead: the same
+sources with -DGINI_DEBUG_CHECKS (device-side index checks that record
+GINI_EINDEX); the binding loads it when GINI_DEBUG=1.
 """
 from __future__ import annotations
 
@@ -19,6 +23,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libginimds.so")
+DEBUG_DIR = os.path.join(HERE, "_build_debug")
+DEBUG_FLAGS = ["-DGINI_DEBUG_CHECKS"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", CSRC, "-I", INCLUDE,
@@ -36,44 +42,49 @@ def _sources():
     return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
 
 
-def _fingerprint() -> str:
+def _fingerprint(flags) -> str:
     h = hashlib.sha256()
     for d in (CSRC, INCLUDE):
         for f in sorted(os.listdir(d)):
             with open(os.path.join(d, f), "rb") as fh:
                 h.update(f.encode())
                 h.update(fh.read())
-    h.update(" ".join(ARCH + FLAGS).encode())
+    h.update(" ".join(ARCH + flags).encode())
     return h.hexdigest()
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
+def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False,
+          debug: bool = False) -> str:
     """Compile if sources changed since the last build; returns the .so path.
     Processes that build at once (one per GPU) take turns on a file lock; the
-    later ones find the stamp current and return."""
+    later ones find the stamp current and return.  debug: the library with
+    device-side index checks, in its own folder."""
     import fcntl
-    os.makedirs(OUT_DIR, exist_ok=True)
-    with open(os.path.join(OUT_DIR, ".lock"), "w") as lock:
+    out = DEBUG_DIR if debug else OUT_DIR
+    os.makedirs(out, exist_ok=True)
+    with open(os.path.join(out, ".lock"), "w") as lock:
         fcntl.flock(lock, fcntl.LOCK_EX)
         try:
-            return _build_locked(force, verbose, ptxas_info)
+            return _build_locked(force, verbose, ptxas_info, out,
+                                 FLAGS + (DEBUG_FLAGS if debug else []))
         finally:
             fcntl.flock(lock, fcntl.LOCK_UN)
 
 
-def _build_locked(force: bool, verbose: bool, ptxas_info: bool) -> str:
-    stamp = os.path.join(OUT_DIR, "stamp")
-    fp = _fingerprint()
-    if not force and os.path.exists(LIB) and os.path.exists(stamp):
+def _build_locked(force: bool, verbose: bool, ptxas_info: bool, out: str, flags) -> str:
+    lib = os.path.join(out, "libginimds.so")
+    stamp = os.path.join(out, "stamp")
+    fp = _fingerprint(flags)
+    if not force and os.path.exists(lib) and os.path.exists(stamp):
         with open(stamp) as f:
             if f.read().strip() == fp:
-                return LIB
+                return lib
     nvcc = _nvcc()
     extra = ["-Xptxas", "-v"] if ptxas_info else []
 
     def compile_one(src):
-        obj = os.path.join(OUT_DIR, os.path.basename(src)[:-3] + ".o")
-        cmd = [nvcc, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
+        obj = os.path.join(out, os.path.basename(src)[:-3] + ".o")
+        cmd = [nvcc, *ARCH, *flags, *extra, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stderr}")
@@ -86,16 +97,17 @@ def _build_locked(force: bool, verbose: bool, ptxas_info: bool) -> str:
         for _, err in results:
             if err:
                 sys.stderr.write(err)
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *[o for o, _ in results]]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib)
     with open(stamp, "w") as f:
         f.write(fp)
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True, ptxas_info="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose=True, ptxas_info="-v" in sys.argv,
+                debug="--debug" in sys.argv))

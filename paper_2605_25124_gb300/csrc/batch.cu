@@ -21,6 +21,7 @@
 #include <string>
 #include <vector>
 
+#define GINI_FILE_ID 3  // site numbers of the debug index checks
 #include "common.cuh"
 
 namespace gini {
@@ -59,6 +60,8 @@ struct BatchParams {
   // k_batch_det_reduce adds them up per point and per fit in a fixed order.
   float* part;
   float* spart;
+  int64_t delta_elems;  // extents of the pool and the point pairs (debug index checks)
+  int64_t pts;
 };
 
 __device__ __forceinline__ int find_seg(const BatchSeg* segs, int nseg, int64_t g) {
@@ -138,11 +141,17 @@ __global__ void __launch_bounds__(TILE / ROWS * 32) k_batch_iter(const BatchPara
         J = 0;
       }
     }
+    if (!(GINI_IDX_OK(B.err, s, B.nseg))) break;  // (debug builds) uniform over the CTA
     const BatchSeg& sg = B.segs[s];
     const int64_t n = sg.n;
     const int64_t i0 = (int64_t)I * TILE, j0 = (int64_t)J * TILE;
     const int64_t t_local = g - sg.tile_begin;
     const int64_t tile_off = sg.delta_off + t_local * (int64_t)(TILE * TILE);
+    // (debug builds) the segment and its tile inside the pool; uniform over
+    // the CTA, so skipping the tile skips its barriers in every thread
+    if (!(GINI_IDX_OK(B.err, t_local, sg.tiles * (sg.tiles + 1) / 2) &&
+          GINI_IDX_OK(B.err, tile_off + TILE * TILE - 1, B.delta_elems)))
+      continue;
     // this thread's ROWS x 4 dissimilarities, kept in registers (as floats)
     // for all restarts
     float4 d[ROWS];
@@ -162,7 +171,8 @@ __global__ void __launch_bounds__(TILE / ROWS * 32) k_batch_iter(const BatchPara
     for (int e = threadIdx.x; e < 2 * R * TILE; e += NT) {
       const int side = e / (R * TILE), rr = (e / TILE) % R, l = e % TILE;
       const int64_t pt = (side ? j0 : i0) + l;  // < npad: padding pairs are zero
-      s_u[side][rr][l] = B.P[sg.pt_off + rr * sg.npad + pt];
+      const int64_t pi = sg.pt_off + rr * sg.npad + pt;
+      s_u[side][rr][l] = GINI_IDX_OK(B.err, pi, B.pts) ? B.P[pi] : make_float2(0.f, 0.f);
     }
     __syncthreads();
     const bool masked = (I == J) || (i0 + TILE > n) || (j0 + TILE > n);
@@ -234,8 +244,12 @@ __global__ void __launch_bounds__(TILE / ROWS * 32) k_batch_iter(const BatchPara
         if (lane < ROWS) {
           const int rl = warp * ROWS + row_of_lane<ROWS>(lane);
           const int64_t gi = i0 + rl;
-          if (B.part) B.part[((g * R + r) * 2) * TILE + rl] = rs;
-          else if (gi < n) atomicAdd(B.h + sg.h_off + r * n + gi, rs);
+          if (B.part) {
+            if (GINI_IDX_OK(B.err, ((g * R + r) * 2) * TILE + rl, B.total_tiles * R * 2 * TILE))
+              B.part[((g * R + r) * 2) * TILE + rl] = rs;
+          } else if (gi < n) {
+            atomicAdd(B.h + sg.h_off + r * n + gi, rs);
+          }
         }
 #pragma unroll
         for (int c = 0; c < 4; ++c) s_col[buf][warp][4 * lane + c] = col[c];
@@ -246,14 +260,22 @@ __global__ void __launch_bounds__(TILE / ROWS * 32) k_batch_iter(const BatchPara
 #pragma unroll
         for (int w = 0; w < WARPS; ++w) v += s_col[buf][w][threadIdx.x];
         const int64_t gj = j0 + threadIdx.x;
-        if (B.part) B.part[((g * R + r) * 2 + 1) * TILE + threadIdx.x] = v;
-        else if (gj < n) atomicAdd(B.h + sg.h_off + r * n + gj, v);
+        if (B.part) {
+          if (GINI_IDX_OK(B.err, ((g * R + r) * 2 + 1) * TILE + threadIdx.x,
+                          B.total_tiles * R * 2 * TILE))
+            B.part[((g * R + r) * 2 + 1) * TILE + threadIdx.x] = v;
+        } else if (gj < n) {
+          atomicAdd(B.h + sg.h_off + r * n + gj, v);
+        }
       }
       if (threadIdx.x == 0) {
         float v = 0.f;
         for (int w = 0; w < WARPS; ++w) v += s_S[buf][w];
-        if (B.spart) B.spart[g * R + r] = v;
-        else atomicAdd(B.acc + sg.fit0 + r, (double)v);
+        if (B.spart) {
+          if (GINI_IDX_OK(B.err, g * R + r, B.total_tiles * R)) B.spart[g * R + r] = v;
+        } else {
+          atomicAdd(B.acc + sg.fit0 + r, (double)v);
+        }
       }
       if constexpr (NBUF == 1) __syncthreads();
     }
@@ -651,6 +673,8 @@ extern "C" int gini_fit_batched(const gini_problem* probs, int nprob, const doub
   P.err = w.err;
   P.part = w.part;
   P.spart = w.spart;
+  P.delta_elems = pl.delta_elems;
+  P.pts = pl.pts;
   const int nseg = (int)pl.segs.size();
   // deterministic mode: h and each fit's stress from the partials of a pass
   auto det_reduce = [&](double* acc) {

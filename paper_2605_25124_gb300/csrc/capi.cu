@@ -4,6 +4,7 @@
 
 #include <atomic>
 
+#define GINI_FILE_ID 5  // site numbers of the debug index checks
 #include "common.cuh"
 
 using namespace gini;
@@ -33,6 +34,7 @@ extern "C" const char* gini_status_str(int status) {
     case GINI_ENOMEM: return "GINI_ENOMEM: workspace too small";
     case GINI_ECUDA: return "GINI_ECUDA: CUDA runtime error";
     case GINI_ETIMEOUT: return "GINI_ETIMEOUT: bounded device wait expired";
+    case GINI_EINDEX: return "GINI_EINDEX: a device-side index check failed (debug build)";
     default: return "unknown gini status";
   }
 }
@@ -88,6 +90,7 @@ extern "C" int gini_check(void* ws, void* stream) {
   if (e == cudaSuccess) e = cudaMemcpy(&word, ws, sizeof(word), cudaMemcpyDeviceToHost);
   if (e == cudaSuccess && word) e = cudaMemset(ws, 0, sizeof(word));
   if (e != cudaSuccess) { gini_set_cuda_error(e); return GINI_ECUDA; }
+  if (word & ERR_INDEX) return GINI_EINDEX;  // debug builds only
   if (word & ERR_TIMEOUT) return GINI_ETIMEOUT;
   if (word & ERR_NONFINITE) return GINI_ENONFINITE;
   return GINI_OK;

@@ -19,13 +19,61 @@ constexpr int TILE = 128;  // edge B of the tiled triangle layout
 // Device-side error bits, OR-ed into the first word of the workspace.
 constexpr unsigned ERR_NONFINITE = 1u;
 constexpr unsigned ERR_TIMEOUT = 2u;
+constexpr unsigned ERR_INDEX = 4u;  // a debug build's index check failed
 
-// The first 256 bytes of every workspace hold the error word.
+// The first 256 bytes of every workspace hold the error word (and, in debug
+// builds, the record of the first failed index check at byte 64).
 constexpr size_t WS_HEADER = 256;
 
 __device__ __forceinline__ void raise_error(unsigned* err, unsigned bit) {
   if (err) atomicOr(err, bit);
 }
+
+// Debug builds (-DGINI_DEBUG_CHECKS) check the offsets the hot kernels compute
+// (rows of X, stored Delta entries and tiles, point arrays, partial buffers,
+// shared-memory slots) against the extents the call's sizes define.  A failed
+// check ORs ERR_INDEX into the error word, keeps the first failure's site
+// (file id x 100000 + line), index and bound in the header's record, counts
+// the failures, and the access it guards is skipped.  Release builds compile
+// every check to `true`, so the kernels are the same as without them.
+struct DebugRecord {
+  unsigned site;
+  unsigned count;
+  long long index;
+  long long bound;
+};
+constexpr size_t DEBUG_RECORD_OFF = 64;
+static_assert(DEBUG_RECORD_OFF + sizeof(DebugRecord) <= WS_HEADER, "record inside the header");
+
+#ifndef GINI_FILE_ID
+#define GINI_FILE_ID 0
+#endif
+
+#ifdef GINI_DEBUG_CHECKS
+static __device__ __noinline__ void index_fail(unsigned* err, unsigned site, long long idx,
+                                               long long bound) {
+  if (!err) return;
+  atomicOr(err, ERR_INDEX);
+  DebugRecord* r = reinterpret_cast<DebugRecord*>(reinterpret_cast<char*>(err) + DEBUG_RECORD_OFF);
+  if (atomicCAS(&r->site, 0u, site) == 0u) {
+    r->index = idx;
+    r->bound = bound;
+  }
+  atomicAdd(&r->count, 1u);
+}
+__device__ __forceinline__ bool idx_ok(unsigned* err, unsigned site, long long idx,
+                                       long long bound) {
+  if (idx >= 0 && idx < bound) return true;
+  index_fail(err, site, idx, bound);
+  return false;
+}
+// true when 0 <= idx < bound; otherwise records the failure and is false
+#define GINI_IDX_OK(err, idx, bound)                                                    \
+  ::gini::idx_ok((err), (unsigned)(GINI_FILE_ID * 100000 + __LINE__), (long long)(idx), \
+                 (long long)(bound))
+#else
+#define GINI_IDX_OK(err, idx, bound) true
+#endif
 
 // Number of tiles along one edge for n points.
 __host__ __device__ __forceinline__ int64_t tiles_1d(int64_t n) { return (n + TILE - 1) / TILE; }

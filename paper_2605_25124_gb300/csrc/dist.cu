@@ -43,6 +43,7 @@
 #include <algorithm>
 #include <vector>
 
+#define GINI_FILE_ID 1  // site numbers of the debug index checks
 #include "common.cuh"
 #include "sortnet.cuh"
 
@@ -104,16 +105,22 @@ __device__ __forceinline__ void add_exact128(unsigned long long* acc, double v, 
 
 __device__ __forceinline__ void store_delta(const DistParams& P, int q, int64_t i, int64_t j,
                                             float d) {
+  // (debug builds) matrix q of the call, 0 <= i < j < n
+  if (!(GINI_IDX_OK(P.err, q, P.n_nu) && GINI_IDX_OK(P.err, j, P.n) && GINI_IDX_OK(P.err, i, j)))
+    return;
   if (P.layout == GINI_LAYOUT_FULL) {
     float* o = reinterpret_cast<float*>(P.out) + (int64_t)q * P.nu_stride;
+    if (!(GINI_IDX_OK(P.err, j, P.ldd))) return;
     o[i * P.ldd + j] = d;
     o[j * P.ldd + i] = d;
     return;
   }
   if (P.layout == LAYOUT_STRIP) {  // FP32 rows 0..n-1 of columns col_begin .. col_begin+ldd-1
+    if (!(GINI_IDX_OK(P.err, j - P.col_begin, P.ldd))) return;
     reinterpret_cast<float*>(P.out)[(int64_t)q * P.nu_stride + i * P.ldd + (j - P.col_begin)] = d;
     return;
   }
+  if (!(GINI_IDX_OK(P.err, tiled_index(i, j, P.tiles), P.plane))) return;
   const int64_t idx = (int64_t)q * P.nu_stride + tiled_index(i, j, P.tiles);
   if (P.dtype == GINI_F32) {
     reinterpret_cast<float*>(P.out)[idx] = d;
@@ -229,7 +236,7 @@ __device__ __forceinline__ void dist_body(const DistParams& P) {
 
   for (int64_t jb = col0; jb < col0 + P.cb; jb += G) {
     const int64_t j = jb + seg;
-    const bool active = row_ok && j > i && j < P.col_end;
+    const bool active = row_ok && j > i && j < P.col_end && GINI_IDX_OK(P.err, j, P.n);
     if (!__any_sync(FULL_MASK, active)) continue;
     float acc[NQ];
 #pragma unroll
@@ -299,9 +306,10 @@ __device__ __forceinline__ void dist_body(const DistParams& P) {
           const float hi = unord_bits((unsigned)(kv[t] >> 32));
           const float w = hi * (float)(pos - s + 1);
           const int a = tab_addr<E>(s + pos);
+          const bool tab_ok = GINI_IDX_OK(P.err, s + pos, 2 * P.m - 1);
 #pragma unroll
           for (int q = 0; q < NQ; ++q)
-            if (q < P.n_nu) acc[q] = fmaf(w, s_tab[q * tab_stride + a], acc[q]);
+            if (q < P.n_nu && tab_ok) acc[q] = fmaf(w, s_tab[q * tab_stride + a], acc[q]);
         }
       }
     }
@@ -427,13 +435,13 @@ __device__ __noinline__ void keyed_fix_run(const DistParams& P, const float* s_t
         lt += __shfl_xor_sync(FULL_MASK, lt, o);
         eq += __shfl_xor_sync(FULL_MASK, eq, o);
       }
-      if (h && ls == 0) {
+      if (h && ls == 0 && GINI_IDX_OK(P.err, 2 * (f + lt) + eq - 1, 2 * P.m - 1)) {
         const int a = tab_addr<E>(2 * (f + lt) + eq - 1);
         for (int q = 0; q < P.n_nu; ++q) corr[q] += val * s_tab[q * tab_stride + a];
       }
     }
   }
-  if (have && ls == 0) {
+  if (have && ls == 0 && GINI_IDX_OK(P.err, 2 * f + c - 1, 2 * P.m - 1)) {
     const int a = tab_addr<E>(2 * f + c - 1);
     for (int q = 0; q < P.n_nu; ++q) corr[q] -= (float)c * val * s_tab[q * tab_stride + a];
   }
@@ -497,7 +505,7 @@ __device__ __forceinline__ void dist_keyed_body(const DistParams& P) {
   const int pos0 = E * ls;
   for (int64_t jb = col0; jb < col0 + P.cb; jb += G) {
     const int64_t j = jb + seg;
-    const bool active = row_ok && j > i && j < P.col_end;
+    const bool active = row_ok && j > i && j < P.col_end && GINI_IDX_OK(P.err, j, P.n);
     if (!__any_sync(FULL_MASK, active)) continue;
     float u[E];
 #pragma unroll
@@ -537,9 +545,10 @@ __device__ __forceinline__ void dist_keyed_body(const DistParams& P) {
         const float fc = __int_as_float(0x4B000000 + cnt) - 8388608.f;  // (float)cnt
         const float w = cell_value(v[t]) * fc;
         const int a = tab_addr<E>(s + pos - 2 * n_lo);
+        const bool tab_ok = GINI_IDX_OK(P.err, s + pos - 2 * n_lo, 2 * P.m - 1);
 #pragma unroll
         for (int q = 0; q < NQ; ++q)
-          if (NQ == 1 || q < P.n_nu) acc[q] = fmaf(w, s_tab[q * tab_stride + a], acc[q]);
+          if ((NQ == 1 || q < P.n_nu) && tab_ok) acc[q] = fmaf(w, s_tab[q * tab_stride + a], acc[q]);
         if (cnt > 1 && (__float_as_uint(v[t]) & 1u)) amb |= 1u << t;
       }
     }
@@ -736,7 +745,7 @@ __global__ void k_strip_scale(unsigned* colmax_bits, int64_t c0, int64_t c1) {
 // tile columns, y: 256-element slice of the tile); one thread per element.
 __global__ void k_strip_quant(const float* __restrict__ strip, int64_t n, int64_t w, int64_t c0,
                               int64_t T, int64_t J0, int64_t nJ, const float* __restrict__ scale,
-                              __nv_fp8_storage_t* __restrict__ out) {
+                              __nv_fp8_storage_t* __restrict__ out, unsigned* err) {
   // tiles (I, J), J0 <= J < J0 + nJ, I <= J: enumerate J-major (column of
   // tiles), I inside; t -> (I, J) by the running count (J + 1 tiles per column)
   int64_t t = blockIdx.x, J = J0;
@@ -747,6 +756,10 @@ __global__ void k_strip_quant(const float* __restrict__ strip, int64_t n, int64_
   const int64_t I = t;
   const int rc = (int)blockIdx.y * blockDim.x + threadIdx.x;
   const int64_t i = I * TILE + rc / TILE, j = J * TILE + rc % TILE;
+  // (debug builds) the tile is in the triangle and the strip holds column j
+  if (!(GINI_IDX_OK(err, tile_offset(I, J, T), T * (T + 1) / 2) &&
+        GINI_IDX_OK(err, I, J + 1) && (j >= n || GINI_IDX_OK(err, j - c0, w))))
+    return;
   const float v = (i < n && j < n && i < j) ? strip[i * w + (j - c0)] : 0.f;
   const float sc = (j < n) ? scale[j] : 1.f;
   out[tile_offset(I, J, T) * (TILE * TILE) + rc] =
@@ -770,7 +783,7 @@ __global__ void __launch_bounds__(LONG_WARPS * 32) k_dist_long(const DistParams 
   const int m = (int)P.m, tab_n = 2 * m - 1;
   const int64_t i = blockIdx.y;
   const int64_t j = std::max(i + 1, P.col_begin) + (int64_t)blockIdx.x * LONG_WARPS + warp;
-  const bool active = i < P.n - 1 && j < P.col_end;
+  const bool active = i < P.n - 1 && j < P.col_end && GINI_IDX_OK(P.err, j, P.n);
   unsigned long long* K = s_long + (size_t)warp * nchunk * LONG_CHUNK_SLOTS;
   const float* xi = P.X + i * P.ldx;
   const float* xj = P.X + (active ? j : i) * P.ldx;
@@ -797,9 +810,11 @@ __global__ void __launch_bounds__(LONG_WARPS * 32) k_dist_long(const DistParams 
                    eq);
       const float hi = two_sum_canonical(a, -b).x;
       const int idx = 2 * lt + eq - 1;
+      const bool tab_ok = GINI_IDX_OK(P.err, idx, tab_n);
 #pragma unroll
       for (int q = 0; q < NU_MAX; ++q)
-        if (q < P.n_nu) acc[q] = fmaf(hi, __ldg(P.wtab + (int64_t)q * tab_n + idx), acc[q]);
+        if (q < P.n_nu && tab_ok)
+          acc[q] = fmaf(hi, __ldg(P.wtab + (int64_t)q * tab_n + idx), acc[q]);
     }
 #pragma unroll
     for (int q = 0; q < NU_MAX; ++q) {
@@ -1034,7 +1049,7 @@ extern "C" int gini_dist(const float* X_dev, int64_t n, int64_t p, int64_t ldx,
           k_strip_scale<<<(unsigned)((c1 - c0 + 255) / 256), 256, 0, s>>>(cm, c0, c1);
           k_strip_quant<<<dim3((unsigned)ntile, TILE * TILE / 256), 256, 0, s>>>(
               sq, n, w, c0, T, J0, nJ, col_scale_dev + (int64_t)q * n,
-              reinterpret_cast<__nv_fp8_storage_t*>(delta_dev) + (int64_t)q * nu_stride);
+              reinterpret_cast<__nv_fp8_storage_t*>(delta_dev) + (int64_t)q * nu_stride, err);
           e = cudaGetLastError();
         }
         (void)plane;

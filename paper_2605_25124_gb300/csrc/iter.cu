@@ -24,6 +24,7 @@
 
 #include <algorithm>
 
+#define GINI_FILE_ID 2  // site numbers of the debug index checks
 #include "common.cuh"
 #include "pipe.cuh"
 
@@ -216,6 +217,7 @@ __global__ void __launch_bounds__(256) k_full(const IterParams Q) {
   const float* D = reinterpret_cast<const float*>(Q.delta);
   double Sd = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * 8 + warp; i < Q.n; i += (int64_t)gridDim.x * 8) {
+    if (!(GINI_IDX_OK(Q.err, Q.n - 1, Q.ldd))) break;  // (debug builds) rows of the n x ldd matrix
     float yi[K];
     float2 Pi[NP];
 #pragma unroll
@@ -308,6 +310,10 @@ __global__ void __launch_bounds__(256) k_full(const IterParams Q) {
 template <int DT>
 __device__ __forceinline__ void load4(const IterParams& Q, int64_t off, float (&d)[4],
                                       const float (&sc)[4]) {
+  if (!(GINI_IDX_OK(Q.err, off + 3, Q.plane))) {  // (debug builds) inside the plane
+    d[0] = d[1] = d[2] = d[3] = 0.f;
+    return;
+  }
   if (DT == GINI_F32) {
     const float4 v = __ldcs(reinterpret_cast<const float4*>(reinterpret_cast<const float*>(Q.delta) + off));
     d[0] = v.x; d[1] = v.y; d[2] = v.z; d[3] = v.w;
@@ -550,15 +556,26 @@ k_fused2(const IterParams Q, int64_t ntiles) {
         if (h == 0 && c > 0) tile_next(I, J, Q.tiles);
         const int64_t eoff = t * (int64_t)(TILE * TILE) + (int64_t)h * CHUNK_ROWS * TILE;
         unsigned char* dst = s_stage + s * C::stage_bytes;
-        mbar_arrive_expect_tx(&bar_full[s], C::stage_bytes);
-        bulk_copy_g2s(dst, base + eoff * C::esize, C::plane_bytes, &bar_full[s]);
-        if (C::planes == 2)
-          bulk_copy_g2s(dst + C::plane_bytes, base + (Q.plane + eoff) * C::esize, C::plane_bytes,
-                        &bar_full[s]);
-        // point arrays are padded to whole tiles, so these stay in bounds
-        bulk_copy_g2s(dst + C::urow_off, Q.P + (int64_t)I * TILE + h * CHUNK_ROWS,
-                      CHUNK_ROWS * 8, &bar_full[s]);
-        bulk_copy_g2s(dst + C::ucol_off, Q.P + (int64_t)J * TILE, TILE * 8, &bar_full[s]);
+        // (debug builds) the chunk inside the plane, the tile's points inside
+        // the padded point array; a failed check completes the stage without
+        // copies, so the consumers compute on stale data but never wait
+        [[maybe_unused]] const int64_t padded = Q.tiles * TILE;
+        if (GINI_IDX_OK(Q.err, eoff + CHUNK_ROWS * TILE - 1, ntiles * (TILE * TILE)) &&
+            GINI_IDX_OK(Q.err, t, ntiles) &&
+            GINI_IDX_OK(Q.err, (int64_t)I * TILE + h * CHUNK_ROWS + CHUNK_ROWS - 1, padded) &&
+            GINI_IDX_OK(Q.err, (int64_t)J * TILE + TILE - 1, padded)) {
+          mbar_arrive_expect_tx(&bar_full[s], C::stage_bytes);
+          bulk_copy_g2s(dst, base + eoff * C::esize, C::plane_bytes, &bar_full[s]);
+          if (C::planes == 2)
+            bulk_copy_g2s(dst + C::plane_bytes, base + (Q.plane + eoff) * C::esize, C::plane_bytes,
+                          &bar_full[s]);
+          // point arrays are padded to whole tiles, so these stay in bounds
+          bulk_copy_g2s(dst + C::urow_off, Q.P + (int64_t)I * TILE + h * CHUNK_ROWS,
+                        CHUNK_ROWS * 8, &bar_full[s]);
+          bulk_copy_g2s(dst + C::ucol_off, Q.P + (int64_t)J * TILE, TILE * 8, &bar_full[s]);
+        } else {
+          mbar_arrive(&bar_full[s]);
+        }
         issued = c + 1;
       }
       // Copies still in flight must land before this CTA's shared memory can
@@ -645,7 +662,9 @@ k_fused2(const IterParams Q, int64_t ntiles) {
       else rowacc0 += rs;
       if (h == 1) {
         const int64_t tcur = t_begin + (c >> 1);
-        if (Q.part && lane < 8) {  // deterministic: this tile's row sums
+        if (Q.part && lane < 8 &&  // deterministic: this tile's row sums
+            GINI_IDX_OK(Q.err, (2 * tcur) * TILE + warp * 8 + rev3(lane) + CHUNK_ROWS,
+                        2 * ntiles * TILE)) {
           float* rp = Q.part + (2 * tcur) * TILE + warp * 8 + rev3(lane);
           rp[0] = rowacc0;
           rp[CHUNK_ROWS] = rowacc1;
@@ -660,8 +679,12 @@ k_fused2(const IterParams Q, int64_t ntiles) {
 #pragma unroll
           for (int w = 0; w < CONSUMER_WARPS; ++w) v += s_colw[(c >> 1) & 1][w][threadIdx.x];
           const int64_t gj = (int64_t)J * TILE + threadIdx.x;
-          if (Q.part) Q.part[(2 * tcur + 1) * TILE + threadIdx.x] = v;
-          else if (gj < n) atomicAdd(Q.h + gj, v);
+          if (Q.part) {
+            if (GINI_IDX_OK(Q.err, (2 * tcur + 1) * TILE + threadIdx.x, 2 * ntiles * TILE))
+              Q.part[(2 * tcur + 1) * TILE + threadIdx.x] = v;
+          } else if (gj < n) {
+            atomicAdd(Q.h + gj, v);
+          }
         }
       }
     }
@@ -897,8 +920,12 @@ __global__ void __launch_bounds__(FUSED_THREADS, 2) k_fusedk(const IterParams Q,
               const int rl = warp * 16 + rb + rev3(lane & 7);
               const int64_t gi = i0 + rl;
               if (lane < 8) {
-                if (Q.part) Q.part[(2 * t * TILE + rl) * K + a] = v;
-                else if (gi < Q.n) atomicAdd(Q.h + gi * K + a, v);
+                if (Q.part) {
+                  if (GINI_IDX_OK(Q.err, (2 * t * TILE + rl) * K + a, 2 * ntiles * TILE * K))
+                    Q.part[(2 * t * TILE + rl) * K + a] = v;
+                } else if (gi < Q.n) {
+                  atomicAdd(Q.h + gi * K + a, v);
+                }
               }
             }
           }
@@ -944,8 +971,12 @@ __global__ void __launch_bounds__(FUSED_THREADS, 2) k_fusedk(const IterParams Q,
             const int rl = warp * 16 + rb + rev3(lane & 7);
             const int64_t gi = i0 + rl;
             if (lane < 8) {
-              if (Q.part) Q.part[(2 * t * TILE + rl) * K + a] = v;
-              else if (gi < Q.n) atomicAdd(Q.h + gi * K + a, v);
+              if (Q.part) {
+                if (GINI_IDX_OK(Q.err, (2 * t * TILE + rl) * K + a, 2 * ntiles * TILE * K))
+                  Q.part[(2 * t * TILE + rl) * K + a] = v;
+              } else if (gi < Q.n) {
+                atomicAdd(Q.h + gi * K + a, v);
+              }
             }
           }
         }
@@ -968,8 +999,10 @@ __global__ void __launch_bounds__(FUSED_THREADS, 2) k_fusedk(const IterParams Q,
             for (int o = 16; o >= 1; o >>= 1) racc[a] += __shfl_xor_sync(FULL_MASK, racc[a], o);
           }
           if (lane == 0 && Q.part) {
+            if (GINI_IDX_OK(Q.err, (2 * t * TILE + rl) * K + K - 1, 2 * ntiles * TILE * K)) {
 #pragma unroll
-            for (int a = 0; a < K; ++a) Q.part[(2 * t * TILE + rl) * K + a] = racc[a];
+              for (int a = 0; a < K; ++a) Q.part[(2 * t * TILE + rl) * K + a] = racc[a];
+            }
           } else if (lane == 0 && gi < Q.n) {
 #pragma unroll
             for (int a = 0; a < K; ++a) atomicAdd(Q.h + gi * K + a, racc[a]);
@@ -990,7 +1023,8 @@ __global__ void __launch_bounds__(FUSED_THREADS, 2) k_fusedk(const IterParams Q,
       for (int e = threadIdx.x; e < TILE * K; e += FUSED_THREADS) {
         float v = 0.f;
         for (int w = 0; w < FUSED_THREADS / 32; ++w) v += det_cols[w * TILE * K + e];
-        Q.part[(2 * t + 1) * TILE * K + e] = v;
+        if (GINI_IDX_OK(Q.err, (2 * t + 1) * TILE * K + e, 2 * ntiles * TILE * K))
+          Q.part[(2 * t + 1) * TILE * K + e] = v;
       }
     } else if (GRAD) {
 #pragma unroll
@@ -1090,16 +1124,22 @@ __global__ void k_finalize_stress(const double* slots, int cnt, double inv_sd2, 
 // g + 8, ... <= I (column sums); the 8 group sums are added in group order.
 __global__ void __launch_bounds__(8 * TILE) k_det_reduce(const float* __restrict__ part,
                                                        int64_t n, int64_t T, int kp,
-                                                       float* __restrict__ h) {
+                                                       float* __restrict__ h, unsigned* err) {
   __shared__ float s_g[8][TILE * KMAX];
   const int64_t I = blockIdx.x;
   const int g = threadIdx.x / TILE, r = threadIdx.x % TILE;
+  if (!(GINI_IDX_OK(err, kp - 1, KMAX) && GINI_IDX_OK(err, I, T))) return;  // (debug builds)
+  [[maybe_unused]] const int64_t lim = T * (T + 1) * TILE * kp;  // the partials of all tiles
   for (int a = 0; a < kp; ++a) {
     float v = 0.f;
-    for (int64_t J = I + g; J < T; J += 8)
-      v += part[(2 * tile_offset(I, J, T) * TILE + r) * kp + a];
-    for (int64_t J = g; J <= I; J += 8)
-      v += part[((2 * tile_offset(J, I, T) + 1) * TILE + r) * kp + a];
+    for (int64_t J = I + g; J < T; J += 8) {
+      const int64_t o = (2 * tile_offset(I, J, T) * TILE + r) * kp + a;
+      if (GINI_IDX_OK(err, o, lim)) v += part[o];
+    }
+    for (int64_t J = g; J <= I; J += 8) {
+      const int64_t o = ((2 * tile_offset(J, I, T) + 1) * TILE + r) * kp + a;
+      if (GINI_IDX_OK(err, o, lim)) v += part[o];
+    }
     s_g[g][r * kp + a] = v;
   }
   __syncthreads();
@@ -1355,7 +1395,7 @@ static void one_pass(int k, int layout, int dtype_eff, bool grad, const IterPara
     if (Q.part) {
       const int kp = scalar2_path(k, Q.metric, Q.loss) ? 1 : k;
       gini_count_launch(1);
-      k_det_reduce<<<(unsigned)Q.tiles, 8 * TILE, 0, s>>>(Q.part, Q.n, Q.tiles, kp, Q.h);
+      k_det_reduce<<<(unsigned)Q.tiles, 8 * TILE, 0, s>>>(Q.part, Q.n, Q.tiles, kp, Q.h, Q.err);
     }
   } else {
     launch_fused<false>(k, dtype_eff, Q, s);

@@ -6,6 +6,7 @@
 // 2R = first + last position of the run + 2 is scattered back to the index.
 // Longer segments (up to 8192) are sorted in chunks and ranked by search
 // (k_rank_long).
+#define GINI_FILE_ID 4  // site numbers of the debug index checks
 #include "common.cuh"
 #include "sortnet.cuh"
 
@@ -56,7 +57,9 @@ k_rank(const float* __restrict__ v, int64_t nseg, int m, int64_t ld, int32_t* __
 #pragma unroll
   for (int t = E - 1; t >= 0; --t) {
     if (t < E - 1) e = eq(key[t], key[t + 1]) ? e : pos0 + t;
-    if (active && pos0 + t < m) out[sidx * m + (int)(key[t] & 0xffffffffu)] = run_lo[t] + e + 2;
+    // (debug builds) a real position holds a real element's index
+    if (active && pos0 + t < m && GINI_IDX_OK(err, (int64_t)(key[t] & 0xffffffffu), m))
+      out[sidx * m + (int)(key[t] & 0xffffffffu)] = run_lo[t] + e + 2;
   }
 }
 
@@ -73,6 +76,7 @@ k_rank_long(const float* __restrict__ v, int64_t nseg, int m, int64_t ld, int nc
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t sidx = (int64_t)blockIdx.x * RANK_LONG_WARPS + warp;
   if (sidx >= nseg) return;  // warp-uniform; no CTA barrier below
+  if (!(GINI_IDX_OK(err, m - 1, (int64_t)nchunk * LONG_CHUNK))) return;  // (debug builds)
   unsigned long long* K = s_rk + (size_t)warp * nchunk * LONG_CHUNK_SLOTS;
   const float* row = v + sidx * ld;
   bool bad = false;
