@@ -176,8 +176,8 @@ __global__ void __launch_bounds__(TILE / ROWS * 32) k_batch_iter(const BatchPara
     }
     __syncthreads();
     const bool masked = (I == J) || (i0 + TILE > n) || (j0 + TILE > n);
-    const float2 k64 = make_float2(0x1p64f, 0x1p64f);
-    const float2 k126 = make_float2(0x1p126f, 0x1p126f);
+    const float2 khi = make_float2(SIGN_HI, SIGN_HI);
+    const float2 kun = make_float2(LO_UNSCALE, LO_UNSCALE);
     const float2 m1 = make_float2(-1.f, -1.f);
     const float2 k2 = make_float2(2.f, 2.f);
     const float2 nc2 = make_float2(-sg.c2, -sg.c2);
@@ -203,15 +203,15 @@ __global__ void __launch_bounds__(TILE / ROWS * 32) k_batch_iter(const BatchPara
 #pragma unroll
         for (int p = 0; p < 2; ++p) {
           const float2 dh = __fadd2_rn(uh2, nuh[p]);
-          const float2 dlo = __fadd2_rn(ul2, nul[p]);
-          const float2 s2 = __fadd2_rn(dh, dlo);
+          const float2 dlo = __fadd2_rn(ul2, nul[p]);  // lo parts scaled by 2^24
+          const float2 s2 = __ffma2_rn(dlo, kun, dh);
           // exact sign of u_i - u_j on the FMA pipe: dh dominates dlo unless it is
-          // zero; the scalings take any nonzero value, subnormals included, to
-          // magnitude >= 2, so the saturating FMA gives 1, 1/2 or 0
-          const float2 b2 = __fmul2_rn(__ffma2_rn(dh, k64, dlo), k126);
+          // zero; 2^126 takes any nonzero a (>= 2^-125 with the scaled lo parts)
+          // to magnitude >= 2, so the saturating FMA gives 1, 1/2 or 0
+          const float2 a2 = __ffma2_rn(dh, khi, dlo);
           // sp = (sigma + 1) / 2 in {0, 1/2, 1}: one saturating FMA per column
-          const float2 sp = make_float2(__saturatef(fmaf(b2.x, 0x1p24f, 0.5f)),
-                                        __saturatef(fmaf(b2.y, 0x1p24f, 0.5f)));
+          const float2 sp = make_float2(__saturatef(fmaf(a2.x, SIGN_SAT, 0.5f)),
+                                        __saturatef(fmaf(a2.y, SIGN_SAT, 0.5f)));
           const float2 sig = __ffma2_rn(sp, k2, m1);  // 2 sp - 1
           float2 rp = __ffma2_rn(nc2, __fmul2_rn(s2, sig), dv[p]);  // r' = delta - c2 |s|
           if (masked) {
@@ -345,7 +345,7 @@ __global__ void k_batch_update(const BatchSeg* segs, int nseg, int R, const int6
     y[0] = y0;
     y[1] = y1;
     *hp = 0.f;
-    P[sg.pt_off + (int64_t)r * sg.npad + i] = two_diff(y0, y1);
+    P[sg.pt_off + (int64_t)r * sg.npad + i] = point_pair(y0, y1);
     bad = !isfinite(y0) || !isfinite(y1);
   }
   if (__any_sync(FULL_MASK, bad) && (threadIdx.x & 31) == 0) raise_error(err, ERR_NONFINITE);
@@ -373,7 +373,7 @@ __global__ void k_batch_init(const BatchSeg* segs, int nseg, int R, const int64_
     float* y = Y + sg.y_off + (int64_t)r * 2 * sg.n + 2 * i;
     y[0] = y0[0];
     y[1] = y0[1];
-    pr = two_diff(y0[0], y0[1]);
+    pr = point_pair(y0[0], y0[1]);
     h[sg.h_off + (int64_t)r * sg.n + i] = 0.f;
   }
   P[sg.pt_off + (int64_t)r * sg.npad + i] = pr;
@@ -546,29 +546,44 @@ static TuneChoice autotune(const BatchPlan& pl, int R, int dtype, const BatchPar
     auto it = g_tune_cache.find(key);
     if (it != g_tune_cache.end()) return it->second;
   }
-  const TuneChoice cands[] = {{16, 1, dtype}, {16, 2, dtype}, {16, 3, dtype}, {8, 1, dtype},
-                              {8, 2, dtype}};
+  // Each candidate's best of three rounds, the rounds interleaved so that a
+  // slow moment of the GPU does not fall on one candidate only; the default
+  // shape (cands[1]) is kept unless another is more than 2 % faster.
+  constexpr int NC = 5, ROUNDS = 3;
+  const TuneChoice cands[NC] = {{16, 1, dtype}, {16, 2, dtype}, {16, 3, dtype}, {8, 1, dtype},
+                                {8, 2, dtype}};
+  float best_of[NC];
+  for (int c = 0; c < NC; ++c) best_of[c] = 1e30f;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  TuneChoice best = cands[1];
-  float best_ms = 1e30f;
-  for (const TuneChoice& c : cands) {
-    launch_iter(c, true, P, s);  // warm
-    cudaEventRecord(e0, s);
-    launch_iter(c, true, P, s);
-    launch_iter(c, true, P, s);
-    cudaEventRecord(e1, s);
-    if (cudaEventSynchronize(e1) != cudaSuccess) break;
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    if (ms < best_ms) {
-      best_ms = ms;
-      best = c;
+  bool ok = true;
+  for (int round = 0; round < ROUNDS && ok; ++round) {
+    for (int c = 0; c < NC && ok; ++c) {
+      launch_iter(cands[c], true, P, s);  // warm
+      cudaEventRecord(e0, s);
+      launch_iter(cands[c], true, P, s);
+      launch_iter(cands[c], true, P, s);
+      cudaEventRecord(e1, s);
+      if (cudaEventSynchronize(e1) != cudaSuccess) {
+        ok = false;
+        break;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      best_of[c] = std::min(best_of[c], ms);
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  TuneChoice best = cands[1];
+  float best_ms = best_of[1] * 0.98f;
+  for (int c = 0; c < NC; ++c) {
+    if (best_of[c] < best_ms) {
+      best_ms = best_of[c];
+      best = cands[c];
+    }
+  }
   std::lock_guard<std::mutex> lock(g_tune_mu);
   g_tune_cache[key] = best;
   return best;

@@ -119,9 +119,30 @@ __device__ __forceinline__ float2 two_diff(float a, float b) {
   return make_float2(s, lo);
 }
 
+// The point pairs of the iteration kernels: u = a - b as (hi, lo * 2^24), with
+// hi + lo = a - b exactly (two_diff).  |lo| <= ulp(hi)/2 <= 2^-24 |hi|, so the
+// scaled part cannot overflow, and scaling by a power of two is exact and
+// keeps the order of the lo parts.  Two pairs' difference is then
+// dh = hi_i - hi_j and dl' = lo'_i - lo'_j = 2^24 fl(lo_i - lo_j):
+//   the value:     fma(dl', 2^-24, dh) = fl(dh + dl), as without the scaling;
+//   the exact sign: a = fma(dh, 2^88, dl') = 2^24 fl(dh 2^64 + dl) (dh decides
+//   when it is not zero, dl when it is), and every nonzero a has magnitude at
+//   least 2^-125, so sat(fma(a, 2^126, 1/2)) is exactly 0, 1/2 or 1 -- one
+//   FMA fewer than scaling a by 2^150 in two steps.
+constexpr float LO_SCALE = 0x1p24f;
+constexpr float LO_UNSCALE = 0x1p-24f;
+constexpr float SIGN_HI = 0x1p88f;    // weight of dh in a
+constexpr float SIGN_SAT = 0x1p126f;  // takes every nonzero a to magnitude >= 2
+
+__device__ __forceinline__ float2 point_pair(float a, float b) {
+  const float2 t = two_diff(a, b);
+  return make_float2(t.x, t.y * LO_SCALE);
+}
+
 // Sign of (p.hi + p.lo) - (q.hi + q.lo) for two exact pairs produced by
-// two_diff (|lo| <= ulp(hi)/2).  Rounding is monotone, so different hi parts
-// already order the exact values; equal hi parts are ordered by lo.
+// two_diff (|lo| <= ulp(hi)/2), or by point_pair (lo scaled).  Rounding is
+// monotone, so different hi parts already order the exact values; equal hi
+// parts are ordered by lo.
 __device__ __forceinline__ int exact_cmp(float2 p, float2 q) {
   if (p.x != q.x) return p.x < q.x ? -1 : 1;
   if (p.y != q.y) return p.y < q.y ? -1 : 1;

@@ -127,7 +127,7 @@ __global__ void k_prep(const float* __restrict__ Y, int64_t n, int64_t npad,
 #pragma unroll
     for (int a = 0; a < K; ++a)
 #pragma unroll
-      for (int b = a + 1; b < K; ++b) P[i * NP + (p++)] = two_diff(y[a], y[b]);
+      for (int b = a + 1; b < K; ++b) P[i * NP + (p++)] = point_pair(y[a], y[b]);
   }
   if (__any_sync(FULL_MASK, bad) && (threadIdx.x & 31) == 0) raise_error(err, ERR_NONFINITE);
 }
@@ -137,8 +137,8 @@ __global__ void k_prep(const float* __restrict__ Y, int64_t n, int64_t npad,
 // k = 2: residual r = 2^{1-nu}|u_i - u_j| - delta and t = r * sign(u_i - u_j).
 __device__ __forceinline__ void pair2(float2 ui, float2 uj, float c2, float delta, float& r,
                                       float& t) {
-  const float dh = ui.x - uj.x, dl = ui.y - uj.y;
-  r = fmaf(c2, fabsf(dh + dl), -delta);
+  const float dh = ui.x - uj.x, dl = ui.y - uj.y;  // dl scaled by 2^24
+  r = fmaf(c2, fabsf(fmaf(dl, LO_UNSCALE, dh)), -delta);
   const float sg = (dh != 0.f) ? dh : dl;  // exact sign of u_i - u_j
   // r * sign(sg): flip r's sign bit by sg's; an exact tie contributes 0
   const float rs = __int_as_float(__float_as_int(r) ^ (__float_as_int(sg) & 0x80000000));
@@ -171,14 +171,14 @@ __device__ __forceinline__ float pair_k(const float* yi, const float* yj, const 
   return d;
 }
 
-// Exact sign of (hi_i - hi_j) + (lo_i - lo_j) for TwoSum pairs, as -1, 0 or 1
-// on the FMA pipe: a = fma(dh, 2^64, dl) has the sign that decides (dl cannot
-// outweigh a non-zero dh; a = dl when dh = 0), and the scalings take any
-// non-zero value, subnormals included, to >= 1 before the saturations.
+// Exact sign of (hi_i - hi_j) + (lo_i - lo_j) for point pairs (lo scaled by
+// 2^24), as -1, 0 or 1 on the FMA pipe: a = fma(dh, 2^88, dl') has the sign
+// that decides (dl cannot outweigh a non-zero dh; a = dl' when dh = 0), and
+// 2^126 takes any non-zero a to >= 2 before the saturations.
 __device__ __forceinline__ float exact_sign(float2 pi, float2 pj) {
-  const float dh = pi.x - pj.x, dl = pi.y - pj.y;
-  const float b = fmaf(dh, 0x1p64f, dl) * 0x1p126f;
-  return __saturatef(b * 0x1p24f) - __saturatef(-b * 0x1p24f);
+  const float dh = pi.x - pj.x, dl = pi.y - pj.y;  // dl scaled by 2^24
+  const float a = fmaf(dh, SIGN_HI, dl);
+  return __saturatef(a * SIGN_SAT) - __saturatef(-a * SIGN_SAT);
 }
 
 // k = 3: with the midrank offsets x_c = R_c - 2 in {0, +-1/2, +-1} (from the
@@ -457,9 +457,10 @@ __device__ __forceinline__ void load4_smem(const unsigned char* stage, int rr, i
 // r' = -r = delta - c2 |s| and t' = -t, so no negations are needed:
 // S += r'^2, the row sum collects t' (negated when flushed) and the column
 // sum, which needs -t, collects t' directly.
-//   sigma: a = fma(dh, 2^64, dl) has the sign of u_i - u_j (dl cannot
-//   outweigh a non-zero dh; a = dl exactly when dh = 0), and
-//   sat(a 2^150 + 1/2) maps it to exactly 0, 1/2 or 1 = (sigma + 1) / 2.
+//   sigma: with the point pairs' lo parts scaled by 2^24 (point_pair),
+//   a = fma(dh, 2^88, dl') has the sign of u_i - u_j (dl cannot outweigh a
+//   non-zero dh; a = dl' exactly when dh = 0), and sat(a 2^126 + 1/2) maps it
+//   to exactly 0, 1/2 or 1 = (sigma + 1) / 2; s = fma(dl', 2^-24, dh).
 template <int DT, bool GRAD, bool MASKED>
 __device__ __forceinline__ void chunk_compute(const unsigned char* stage, int rbase, int lane,
                                               const float2 (&nuh)[2], const float2 (&nul)[2],
@@ -467,8 +468,8 @@ __device__ __forceinline__ void chunk_compute(const unsigned char* stage, int rb
                                               float2& S2, float2 (&col2)[2], float (&rowv)[8],
                                               int64_t gi0, int64_t gj0, int64_t n, bool diag,
                                               int rl0) {
-  const float2 k64 = make_float2(0x1p64f, 0x1p64f);
-  const float2 k126 = make_float2(0x1p126f, 0x1p126f);
+  const float2 khi = make_float2(SIGN_HI, SIGN_HI);
+  const float2 kun = make_float2(LO_UNSCALE, LO_UNSCALE);
   const float2 m1 = make_float2(-1.f, -1.f);
   const float2 k2 = make_float2(2.f, 2.f);
   const float2 nc2 = make_float2(-c2, -c2);
@@ -483,12 +484,12 @@ __device__ __forceinline__ void chunk_compute(const unsigned char* stage, int rb
     for (int p = 0; p < 2; ++p) {
       const float2 d2 = make_float2(dl[2 * p], dl[2 * p + 1]);
       const float2 dh = __fadd2_rn(uh2, nuh[p]);
-      const float2 dlo = __fadd2_rn(ul2, nul[p]);
-      const float2 s2 = __fadd2_rn(dh, dlo);
-      const float2 b2 = __fmul2_rn(__ffma2_rn(dh, k64, dlo), k126);
+      const float2 dlo = __fadd2_rn(ul2, nul[p]);  // scaled by 2^24
+      const float2 s2 = __ffma2_rn(dlo, kun, dh);
+      const float2 a2 = __ffma2_rn(dh, khi, dlo);
       // sp = (sigma + 1) / 2 in {0, 1/2, 1}: one saturating FMA per column
-      const float2 sp = make_float2(__saturatef(fmaf(b2.x, 0x1p24f, 0.5f)),
-                                    __saturatef(fmaf(b2.y, 0x1p24f, 0.5f)));
+      const float2 sp = make_float2(__saturatef(fmaf(a2.x, SIGN_SAT, 0.5f)),
+                                    __saturatef(fmaf(a2.y, SIGN_SAT, 0.5f)));
       const float2 sig = __ffma2_rn(sp, k2, m1);  // 2 sp - 1
       float2 rp = __ffma2_rn(nc2, __fmul2_rn(s2, sig), d2);  // r' = delta - c2 |s|
       if (MASKED) {
@@ -833,7 +834,8 @@ __global__ void __launch_bounds__(FUSED_THREADS, 2) k_fusedk(const IterParams Q,
       if constexpr (K == 3 && GK) {
         // k = 3, Gini metric, Kruskal loss: two columns per packed f32x2
         // instruction.  For a rank comparison with exact sign sigma,
-        // sp = sat(a 2^150 + 1/2) = (sigma + 1) / 2 in one saturating FMA, and
+        // sp = sat(a 2^126 + 1/2) = (sigma + 1) / 2 in one saturating FMA
+        // (a = fma(dh, 2^88, dl') on the scaled point pairs, point_pair), and
         // the midrank offsets x_c = R_c - 2 are affine in the three sp.  The
         // residual is carried negated, nr = delta - d: S += nr^2, and the row
         // and column sums of dd/dy weighted by r both collect nr * dw (the row
@@ -841,7 +843,7 @@ __global__ void __launch_bounds__(FUSED_THREADS, 2) k_fusedk(const IterParams Q,
         const float t1 = s_w[4], th = s_w[3];
         const float A = (8.f * th - t1) * (1.f / 3.f), B = (4.f * t1 - 8.f * th) * (1.f / 3.f);
         const float2 A2 = make_float2(A, A), B2 = make_float2(B, B);
-        const float2 k64 = make_float2(0x1p64f, 0x1p64f), k126 = make_float2(0x1p126f, 0x1p126f);
+        const float2 khi = make_float2(SIGN_HI, SIGN_HI);
         const float2 m1 = make_float2(-1.f, -1.f), one2 = make_float2(1.f, 1.f);
         float2 ncy[2][3], nch[2][3], ncl[2][3], cacc[2][3];
 #pragma unroll
@@ -879,9 +881,9 @@ __global__ void __launch_bounds__(FUSED_THREADS, 2) k_fusedk(const IterParams Q,
               for (int qq = 0; qq < 3; ++qq) {
                 const float2 dh = __fadd2_rn(rph[qq], nch[p][qq]);
                 const float2 dlo = __fadd2_rn(rpl[qq], ncl[p][qq]);
-                const float2 b = __fmul2_rn(__ffma2_rn(dh, k64, dlo), k126);
-                sp[qq] = make_float2(__saturatef(fmaf(b.x, 0x1p24f, 0.5f)),
-                                     __saturatef(fmaf(b.y, 0x1p24f, 0.5f)));
+                const float2 a = __ffma2_rn(dh, khi, dlo);  // dlo scaled by 2^24
+                sp[qq] = make_float2(__saturatef(fmaf(a.x, SIGN_SAT, 0.5f)),
+                                     __saturatef(fmaf(a.y, SIGN_SAT, 0.5f)));
               }
               float2 xs[3];
               xs[0] = __fadd2_rn(__fadd2_rn(sp[0], sp[1]), m1);  // (s01 + s02) / 2
@@ -1080,7 +1082,7 @@ __global__ void k_update(float* __restrict__ Y, int64_t n, float2* __restrict__ 
 #pragma unroll
     for (int a = 0; a < K; ++a)
 #pragma unroll
-      for (int b = a + 1; b < K; ++b) P[i * NP + (p++)] = two_diff(y[a], y[b]);
+      for (int b = a + 1; b < K; ++b) P[i * NP + (p++)] = point_pair(y[a], y[b]);
   }
   if (__any_sync(FULL_MASK, bad) && (threadIdx.x & 31) == 0) raise_error(err, ERR_NONFINITE);
 }

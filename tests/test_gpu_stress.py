@@ -181,3 +181,46 @@ def test_bounded_wait_expires_and_context_survives(G):
     Dq = quantize(D, "f32")
     Sref, _ = orc.stress_grad(Y.astype(np.float64), 2.0, np.triu(Dq, 1) + np.triu(Dq, 1).T, sd2)
     assert float(S) == pytest.approx(Sref, rel=1e-5)
+
+
+def _tiny_lo_points(k):
+    """Points whose pair differences u = y_a - y_b share their FP32 part and
+    differ only below it (lo parts 2^-30, 2^-140 and subnormal 2^-149 apart),
+    plus exact duplicates: the rank comparisons are decided by lo, or tie."""
+    n = 64
+    Y = np.zeros((n, k), np.float64)
+    for g, (c, eps) in enumerate(((1.0, 2.0 ** -30), (2.0 ** -100, 2.0 ** -140),
+                                  (2.0 ** -120, 2.0 ** -149))):
+        for m in range(16):
+            row = [c, m * eps] if k == 2 else [c, m * eps, (15 - m + 3 * g) * eps]
+            Y[16 * g + m] = row
+    Y[48:] = Y[:16]
+    assert np.array_equal(Y.astype(np.float32).astype(np.float64), Y)  # exact in FP32
+    return Y.astype(np.float32)
+
+
+@pytest.mark.parametrize("k", [2, 3])
+def test_exact_sign_decided_by_tiny_lo_parts(G, k):
+    # The fused and plain kernels order u_i - u_j through TwoSum pairs whose lo
+    # parts carry the sign when the FP32 parts are equal.  Here 3/4 of the
+    # within-group pairs differ only in lo (down to the subnormal step) and a
+    # quarter of the points are exact duplicates (sign 0): a wrong or missing
+    # sign moves h_i by about one delta, about 1/n of the largest gradient.
+    n, nu = 64, 1.7
+    X, D, sd2 = _ref_delta(n, 6, nu, seed=270 + k)
+    Y = _tiny_lo_points(k)
+    Dq = quantize(D, "f32")
+    Dq = np.triu(Dq, 1) + np.triu(Dq, 1).T
+    Sref, gref = orc.stress_grad(Y.astype(np.float64), nu, Dq, sd2)
+    for form in ("f32", "full"):
+        S, g = G.gini_stress_grad(torch.from_numpy(Y).cuda(), nu, _dis(G, D, n, form, sd2))
+        assert float(S) == pytest.approx(Sref, rel=1e-5), form
+        assert np.max(np.abs(g.cpu().numpy() - gref)) <= 1e-5 * np.abs(gref).max(), form
+    if k == 2:  # the batched kernel's own copy of the pair arithmetic: one step
+        eta = orc.default_step(n, 2, nu, sd2, 1.0)
+        y1, h = orc.fit(D, nu, sd2, Y.astype(np.float64), eta, 1)
+        out = G.gini_fit_batched([torch.from_numpy(X).cuda()], [nu], 1, 1,
+                                 torch.from_numpy(Y.reshape(-1)).cuda(), eta0=1.0, history=True)
+        assert out["history"][0, 0, 0, 0].item() == pytest.approx(h[0], rel=1e-5)
+        step = out["Y"].cpu().numpy().reshape(n, 2).astype(np.float64) - Y
+        assert np.max(np.abs(step - (y1 - Y))) <= 1e-5 * np.abs(y1 - Y).max() + 2e-7 * np.abs(Y).max()
