@@ -111,7 +111,8 @@ __device__ __forceinline__ int row_of_lane(int lane) {
 // warps per CTA; lane l takes columns 4l .. 4l+3.  GRAD = false is the final
 // stress-only pass.
 template <int ROWS, bool GRAD, int DT>
-__global__ void __launch_bounds__(TILE / ROWS * 32) k_batch_iter(const BatchParams B) {
+__global__ void __launch_bounds__(TILE / ROWS * 32, ROWS == 16 ? 2 : 0)
+k_batch_iter(const BatchParams B) {  // held to 128 registers: two 16-row CTAs per SM
   constexpr int WARPS = TILE / ROWS;
   constexpr int NT = WARPS * 32;
   __shared__ float2 s_u[2][BATCH_RMAX][TILE];  // [rows | cols][restart][point]

@@ -719,7 +719,7 @@ struct FusedKSmem {
 
 // GK: Gini metric and Kruskal loss only (the other branches compiled out, so the
 // unrolled body stays small enough for the instruction cache).
-template <int K, int DT, bool GRAD, bool GK>
+template <int K, int DT, bool GRAD, bool GK, bool AFF = false>
 __global__ void __launch_bounds__(FUSED_THREADS, 2) k_fusedk(const IterParams Q, int64_t ntiles) {
   constexpr int NP = K * (K - 1) / 2;
   extern __shared__ __align__(16) unsigned char s_raw[];
@@ -842,7 +842,7 @@ __global__ void __launch_bounds__(FUSED_THREADS, 2) k_fusedk(const IterParams Q,
         // sum negated when it is flushed, the column sum needs -r dw).
         const float t1 = s_w[4], th = s_w[3];
         const float A = (8.f * th - t1) * (1.f / 3.f), B = (4.f * t1 - 8.f * th) * (1.f / 3.f);
-        const float2 A2 = make_float2(A, A), B2 = make_float2(B, B);
+        const float2 A2 = make_float2(A, A), B2 = make_float2(B, B), nA2 = make_float2(-A, -A);
         const float2 khi = make_float2(SIGN_HI, SIGN_HI);
         const float2 m1 = make_float2(-1.f, -1.f), one2 = make_float2(1.f, 1.f);
         float2 ncy[2][3], nch[2][3], ncl[2][3], cacc[2][3];
@@ -885,17 +885,26 @@ __global__ void __launch_bounds__(FUSED_THREADS, 2) k_fusedk(const IterParams Q,
                 sp[qq] = make_float2(__saturatef(fmaf(a.x, SIGN_SAT, 0.5f)),
                                      __saturatef(fmaf(a.y, SIGN_SAT, 0.5f)));
               }
-              float2 xs[3];
-              xs[0] = __fadd2_rn(__fadd2_rn(sp[0], sp[1]), m1);  // (s01 + s02) / 2
-              xs[1] = __ffma2_rn(sp[0], m1, sp[2]);              // (s12 - s01) / 2
-              xs[2] = __ffma2_rn(__fadd2_rn(sp[1], sp[2]), m1, one2);  // -(s02 + s12) / 2
               float2 dw[3];
+              if constexpr (AFF) {
+                // B = 0 (a table affine in the rank: nu = 2 or 3): dw_c = A x_c,
+                // formed from the sp in one FMA each.  x_c is in {0, +-1/2, +-1},
+                // so A x_c is exact and these are the general form's bits.
+                dw[0] = __ffma2_rn(__fadd2_rn(sp[0], sp[1]), A2, nA2);  // A (sp0 + sp1 - 1)
+                dw[1] = __fmul2_rn(__ffma2_rn(sp[0], m1, sp[2]), A2);   // A (sp2 - sp0)
+                dw[2] = __ffma2_rn(__fadd2_rn(sp[1], sp[2]), nA2, A2);  // A (1 - sp1 - sp2)
+              } else {
+                float2 xs[3];
+                xs[0] = __fadd2_rn(__fadd2_rn(sp[0], sp[1]), m1);  // (s01 + s02) / 2
+                xs[1] = __ffma2_rn(sp[0], m1, sp[2]);              // (s12 - s01) / 2
+                xs[2] = __ffma2_rn(__fadd2_rn(sp[1], sp[2]), m1, one2);  // -(s02 + s12) / 2
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                  dw[c] = __fmul2_rn(xs[c], __ffma2_rn(B2, __fmul2_rn(xs[c], xs[c]), A2));
+              }
               float2 d = make_float2(0.f, 0.f);
 #pragma unroll
-              for (int c = 0; c < 3; ++c) {
-                dw[c] = __fmul2_rn(xs[c], __ffma2_rn(B2, __fmul2_rn(xs[c], xs[c]), A2));
-                d = __ffma2_rn(__fadd2_rn(ryy[c], ncy[p][c]), dw[c], d);
-              }
+              for (int c = 0; c < 3; ++c) d = __ffma2_rn(__fadd2_rn(ryy[c], ncy[p][c]), dw[c], d);
               float2 nr = __ffma2_rn(d, m1, make_float2(dl[2 * p], dl[2 * p + 1]));
               if (masked) {
                 const int cl = 4 * lane + 2 * p;
@@ -1313,16 +1322,16 @@ static void full_k(int k, const IterParams& Q, cudaStream_t s) {
   }
 }
 
-template <int K, int DT, bool GRAD, bool GK = false>
+template <int K, int DT, bool GRAD, bool GK = false, bool AFF = false>
 static void launch_fusedk(unsigned g, const IterParams& Q, int64_t ntiles, cudaStream_t s) {
   // deterministic mode: per-warp column sums after the staged points
   const size_t smem = sizeof(FusedKSmem<K>) +
                       (GRAD && Q.part ? sizeof(float) * (FUSED_THREADS / 32) * TILE * K : 0);
   if (smem + 1024 > 48 * 1024)  // plus the kernel's static shared memory
-    cudaFuncSetAttribute(k_fusedk<K, DT, GRAD, GK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_fusedk<K, DT, GRAD, GK, AFF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
   gini_count_launch(1);
-  k_fusedk<K, DT, GRAD, GK><<<g, FUSED_THREADS, smem, s>>>(Q, ntiles);
+  k_fusedk<K, DT, GRAD, GK, AFF><<<g, FUSED_THREADS, smem, s>>>(Q, ntiles);
 }
 
 template <int DT, bool GRAD>
@@ -1334,9 +1343,14 @@ static void launch_fused_dt(int k, const IterParams& Q, cudaStream_t s) {
     switch (k) {
       case 2: launch_fusedk<2, DT, GRAD>(g, Q, ntiles, s); return;
       case 3:
-        if (Q.metric == GINI_METRIC_GINI && Q.loss == GINI_LOSS_KRUSKAL)
-          launch_fusedk<3, DT, GRAD, true>(g, Q, ntiles, s);
-        else
+        if (Q.metric == GINI_METRIC_GINI && Q.loss == GINI_LOSS_KRUSKAL) {
+          // the table's cubic term B = (4 T(1) - 8 T(1/2)) / 3 is exactly zero
+          // when T(1) = 2 T(1/2) in FP32 (nu = 2 or 3)
+          if (Q.tab.w[4] == 2.f * Q.tab.w[3])
+            launch_fusedk<3, DT, GRAD, true, true>(g, Q, ntiles, s);
+          else
+            launch_fusedk<3, DT, GRAD, true>(g, Q, ntiles, s);
+        } else
           launch_fusedk<3, DT, GRAD>(g, Q, ntiles, s);
         return;
       case 4: launch_fusedk<4, DT, GRAD>(g, Q, ntiles, s); return;

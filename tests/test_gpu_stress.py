@@ -199,14 +199,14 @@ def _tiny_lo_points(k):
     return Y.astype(np.float32)
 
 
-@pytest.mark.parametrize("k", [2, 3])
-def test_exact_sign_decided_by_tiny_lo_parts(G, k):
+@pytest.mark.parametrize("k,nu", [(2, 1.7), (3, 1.7), (3, 2.0)])  # 2.0: k = 3's affine body
+def test_exact_sign_decided_by_tiny_lo_parts(G, k, nu):
     # The fused and plain kernels order u_i - u_j through TwoSum pairs whose lo
     # parts carry the sign when the FP32 parts are equal.  Here 3/4 of the
     # within-group pairs differ only in lo (down to the subnormal step) and a
     # quarter of the points are exact duplicates (sign 0): a wrong or missing
     # sign moves h_i by about one delta, about 1/n of the largest gradient.
-    n, nu = 64, 1.7
+    n = 64
     X, D, sd2 = _ref_delta(n, 6, nu, seed=270 + k)
     Y = _tiny_lo_points(k)
     Dq = quantize(D, "f32")
