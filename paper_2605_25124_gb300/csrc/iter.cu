@@ -46,6 +46,7 @@ struct IterParams {
   int64_t n;
   const float2* P;  // per point: k = 2 -> u_i as (hi, lo); else the k(k-1)/2 pairs y_ia - y_ib
   const float* Y;   // n x k (generic-k kernels read coordinates)
+  const float4* Y4; // k = 3: y as (y0, y1, y2, 0), padded to whole tiles with zeros (else null)
   const void* delta;
   int64_t ldd;
   const float* col_scale;
@@ -108,13 +109,14 @@ __device__ __forceinline__ void loss_terms(int loss, float d, float delta, float
 
 template <int K>
 __global__ void k_prep(const float* __restrict__ Y, int64_t n, int64_t npad,
-                       float2* __restrict__ P, unsigned* err) {
+                       float2* __restrict__ P, float4* __restrict__ Y4, unsigned* err) {
   constexpr int NP = K * (K - 1) / 2;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   bool bad = false;
   if (i >= n && i < npad) {
 #pragma unroll
     for (int p = 0; p < NP; ++p) P[i * NP + p] = make_float2(0.f, 0.f);
+    if (K == 3 && Y4) Y4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
   if (i < n) {
     float y[K];
@@ -128,6 +130,7 @@ __global__ void k_prep(const float* __restrict__ Y, int64_t n, int64_t npad,
     for (int a = 0; a < K; ++a)
 #pragma unroll
       for (int b = a + 1; b < K; ++b) P[i * NP + (p++)] = point_pair(y[a], y[b]);
+    if (K == 3 && Y4) Y4[i] = make_float4(y[0], y[1], y[K - 1], 0.f);
   }
   if (__any_sync(FULL_MASK, bad) && (threadIdx.x & 31) == 0) raise_error(err, ERR_NONFINITE);
 }
@@ -1055,14 +1058,328 @@ __global__ void __launch_bounds__(FUSED_THREADS, 2) k_fusedk(const IterParams Q,
   block_store_stress(Sd, Q.stress);
 }
 
+// k = 3, Gini metric, Kruskal loss: the fused iteration fed by bulk copies.
+//
+// The arithmetic per pair is k_fusedk's packed k = 3 body (two columns per
+// f32x2 instruction; exact signs of the three coordinate-pair differences from
+// the scaled point pairs; midrank offsets x_c affine in the signs; dw_c =
+// x_c (A + B x_c^2), or A x_c when B = 0).  What changes is how the data
+// arrive.  A CTA owns a contiguous range of tiles, streamed as chunks of 64
+// rows x 128 columns; a stage of the shared-memory ring holds one chunk's
+// dissimilarities, its 64 row points and the tile's 128 column points (padded
+// coordinates Y4 and point pairs P, both padded to whole tiles), all brought
+// by cp.async.bulk and completed on the stage's mbarrier.  There is no
+// producer warp (its registers would cost the second CTA per SM at 128 per
+// thread): each warp counts itself done with a stage in a shared counter, and
+// the warp that completes the count issues the stage's next chunk.  Column
+// sums of a tile meet in per-warp slices behind one named barrier (slices
+// double-buffered by tile parity); row sums of the 8 rows a warp owns in a
+// chunk meet by a transpose-reduction and stay in registers while the tile
+// row does not change.
+template <int DT>
+struct Pipe3Cfg {
+  static constexpr int planes = DT == GINI_BF16X2 ? 2 : 1;
+  static constexpr int esize = DT == GINI_F32 ? 4 : (DT == GINI_FP8E4M3 ? 1 : 2);
+  static constexpr int plane_bytes = CHUNK_ROWS * TILE * esize;
+  static constexpr int yrow_off = planes * plane_bytes;          // 64 x float4
+  static constexpr int prow_off = yrow_off + CHUNK_ROWS * 16;     // 64 x 3 float2
+  static constexpr int ycol_off = prow_off + CHUNK_ROWS * 24;     // 128 x float4
+  static constexpr int pcol_off = ycol_off + TILE * 16;           // 128 x 3 float2
+  static constexpr int stage_bytes = pcol_off + TILE * 24;
+  // ~86 KB of stages + 24.6 KB of column slices keeps two CTAs on an SM
+  static constexpr int stages_raw = (86 * 1024) / stage_bytes;
+  static constexpr int stages = stages_raw > 4 ? 4 : (stages_raw < 2 ? 2 : stages_raw);
+  static constexpr int smem = stages * stage_bytes;
+  static_assert(prow_off % 16 == 0 && ycol_off % 16 == 0 && pcol_off % 16 == 0 &&
+                    stage_bytes % 16 == 0,
+                "bulk-copy destinations must be 16-byte aligned");
+};
+
+// Issues chunk c (tile t = t_begin + c / 2, half h = c & 1, tile (I, J)) into
+// its stage.  One thread.
+template <int DT>
+__device__ __forceinline__ void fused3_issue(const IterParams& Q, unsigned char* s_stage,
+                                             uint64_t* bar_full, int S, int64_t t_begin,
+                                             int64_t ntiles, int c, int I, int J) {
+  using C = Pipe3Cfg<DT>;
+  const int s = c % S, h = c & 1;
+  const int64_t t = t_begin + c / 2;
+  const int64_t eoff = t * (int64_t)(TILE * TILE) + (int64_t)h * CHUNK_ROWS * TILE;
+  const int64_t ri = (int64_t)I * TILE + h * CHUNK_ROWS, cj = (int64_t)J * TILE;
+  unsigned char* dst = s_stage + s * C::stage_bytes;
+  const unsigned char* base = reinterpret_cast<const unsigned char*>(Q.delta);
+  [[maybe_unused]] const int64_t padded = Q.tiles * TILE;
+  // (debug builds) the chunk inside the plane, the points inside the padded
+  // arrays; a failed check completes the stage without copies
+  if (GINI_IDX_OK(Q.err, t, ntiles) &&
+      GINI_IDX_OK(Q.err, eoff + CHUNK_ROWS * TILE - 1, ntiles * (TILE * TILE)) &&
+      GINI_IDX_OK(Q.err, ri + CHUNK_ROWS - 1, padded) && GINI_IDX_OK(Q.err, cj + TILE - 1, padded)) {
+    mbar_arrive_expect_tx(&bar_full[s], C::stage_bytes);
+    bulk_copy_g2s(dst, base + eoff * C::esize, C::plane_bytes, &bar_full[s]);
+    if (C::planes == 2)
+      bulk_copy_g2s(dst + C::plane_bytes, base + (Q.plane + eoff) * C::esize, C::plane_bytes,
+                    &bar_full[s]);
+    bulk_copy_g2s(dst + C::yrow_off, Q.Y4 + ri, CHUNK_ROWS * 16, &bar_full[s]);
+    bulk_copy_g2s(dst + C::prow_off, Q.P + ri * 3, CHUNK_ROWS * 24, &bar_full[s]);
+    bulk_copy_g2s(dst + C::ycol_off, Q.Y4 + cj, TILE * 16, &bar_full[s]);
+    bulk_copy_g2s(dst + C::pcol_off, Q.P + cj * 3, TILE * 24, &bar_full[s]);
+  } else {
+    mbar_arrive(&bar_full[s]);
+  }
+}
+
+template <int DT, bool GRAD, bool AFF>
+__global__ void __launch_bounds__(FUSED_THREADS, 2) k_fused3(const IterParams Q, int64_t ntiles) {
+  using C = Pipe3Cfg<DT>;
+  constexpr int S = C::stages;
+  constexpr int WARPS = FUSED_THREADS / 32;
+  extern __shared__ __align__(128) unsigned char s_stage[];
+  __shared__ __align__(8) uint64_t bar_full[S];
+  __shared__ unsigned s_done[S];  // warps finished with the chunk now in the stage
+  __shared__ float s_colw[2][WARPS][TILE * 3];
+  __shared__ int s_abort;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t n = Q.n;
+  const int64_t t_begin = ntiles * blockIdx.x / gridDim.x;
+  const int64_t t_end = ntiles * (blockIdx.x + 1) / gridDim.x;
+  const int nchunks = (int)(t_end - t_begin) * 2;
+  int I = 0, J = 0;
+  if (nchunks) tile_decode(t_begin, Q.tiles, I, J);
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < S; ++st) {
+      mbar_init(&bar_full[st], 1);
+      s_done[st] = 0;
+    }
+    s_abort = 0;
+    mbar_init_fence();
+  }
+  __syncthreads();
+  volatile int* abort = &s_abort;
+  if (threadIdx.x == 0) {  // the first S chunks
+    int i2 = I, j2 = J;
+    for (int c = 0; c < S && c < nchunks; ++c) {
+      if (c > 0 && (c & 1) == 0) tile_next(i2, j2, Q.tiles);
+      fused3_issue<DT>(Q, s_stage, bar_full, S, t_begin, ntiles, c, i2, j2);
+    }
+  }
+
+  const float t1 = Q.tab.w[4], th = Q.tab.w[3];
+  const float A = (8.f * th - t1) * (1.f / 3.f), B = (4.f * t1 - 8.f * th) * (1.f / 3.f);
+  const float2 A2 = make_float2(A, A), B2 = make_float2(B, B), nA2 = make_float2(-A, -A);
+  const float2 khi = make_float2(SIGN_HI, SIGN_HI);
+  const float2 m1 = make_float2(-1.f, -1.f), one2 = make_float2(1.f, 1.f);
+  float Ssum = 0.f, Scomp = 0.f;  // compensated sum of the per-tile FP32 partials
+  float2 S2 = make_float2(0.f, 0.f);
+  float rowacc[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};  // lane < 8: rows rev3(lane)
+  int curI = -1;
+  float2 ncy[2][3], nch[2][3], ncl[2][3], cacc[2][3];
+  float sc[4] = {1.f, 1.f, 1.f, 1.f};
+  for (int c = 0; c < nchunks; ++c) {
+    const int s = c % S, h = c & 1;
+    if (h == 0 && c > 0) tile_next(I, J, Q.tiles);
+    if (GRAD && h == 0 && I != curI) {
+      if (!Q.part && curI >= 0 && lane < 8) {
+        const int64_t gi = (int64_t)curI * TILE + warp * 8 + rev3(lane);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          if (gi < n) atomicAdd(Q.h + gi * 3 + a, rowacc[0][a]);
+          if (gi + CHUNK_ROWS < n) atomicAdd(Q.h + (gi + CHUNK_ROWS) * 3 + a, rowacc[1][a]);
+        }
+      }
+#pragma unroll
+      for (int a = 0; a < 3; ++a) rowacc[0][a] = rowacc[1][a] = 0.f;
+      curI = I;
+    }
+    if (!mbar_wait_bounded(&bar_full[s], (c / S) & 1, abort)) {
+      raise_error(Q.err, ERR_TIMEOUT);
+      *abort = 1;
+    }
+    const unsigned char* stage = s_stage + s * C::stage_bytes;
+    if (h == 0) {
+      // the lane's four columns (4 lane + 2p, 4 lane + 2p + 1), negated and packed
+      const float4* yc = reinterpret_cast<const float4*>(stage + C::ycol_off);
+      const float2* pc = reinterpret_cast<const float2*>(stage + C::pcol_off);
+#pragma unroll
+      for (int p = 0; p < 2; ++p) {
+        const int c0 = 4 * lane + 2 * p;
+        const float4 ya = yc[c0], yb = yc[c0 + 1];
+        ncy[p][0] = make_float2(-ya.x, -yb.x);
+        ncy[p][1] = make_float2(-ya.y, -yb.y);
+        ncy[p][2] = make_float2(-ya.z, -yb.z);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          const float2 pa = pc[c0 * 3 + a], pb = pc[(c0 + 1) * 3 + a];
+          nch[p][a] = make_float2(-pa.x, -pb.x);
+          ncl[p][a] = make_float2(-pa.y, -pb.y);
+          cacc[p][a] = make_float2(0.f, 0.f);
+        }
+      }
+      if (DT == GINI_FP8E4M3) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int64_t gj = (int64_t)J * TILE + 4 * lane + q;
+          sc[q] = Q.col_scale[gj < n ? gj : n - 1];
+        }
+      }
+    }
+    const bool masked = (I == J) || ((int64_t)I * TILE + TILE > n) || ((int64_t)J * TILE + TILE > n);
+    const float4* yr = reinterpret_cast<const float4*>(stage + C::yrow_off);
+    const float2* pr = reinterpret_cast<const float2*>(stage + C::prow_off);
+    float racc8[3][8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int rr = warp * 8 + q;  // row within the chunk
+      const int rl = h * CHUNK_ROWS + rr;
+      float dl[4];
+      load4_smem<DT>(stage, rr, lane, dl, sc);
+      const float4 yv = yr[rr];
+      const float yvs[3] = {yv.x, yv.y, yv.z};
+      float2 ryy[3], rph[3], rpl[3], rn[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const float2 pv = pr[rr * 3 + a];
+        ryy[a] = make_float2(yvs[a], yvs[a]);
+        rph[a] = make_float2(pv.x, pv.x);
+        rpl[a] = make_float2(pv.y, pv.y);
+        rn[a] = make_float2(0.f, 0.f);
+      }
+#pragma unroll
+      for (int p = 0; p < 2; ++p) {
+        float2 sp[3];
+#pragma unroll
+        for (int qq = 0; qq < 3; ++qq) {
+          const float2 dh = __fadd2_rn(rph[qq], nch[p][qq]);
+          const float2 dlo = __fadd2_rn(rpl[qq], ncl[p][qq]);
+          const float2 a2 = __ffma2_rn(dh, khi, dlo);  // dlo scaled by 2^24
+          sp[qq] = make_float2(__saturatef(fmaf(a2.x, SIGN_SAT, 0.5f)),
+                               __saturatef(fmaf(a2.y, SIGN_SAT, 0.5f)));
+        }
+        float2 dw[3];
+        if constexpr (AFF) {
+          dw[0] = __ffma2_rn(__fadd2_rn(sp[0], sp[1]), A2, nA2);  // A (sp0 + sp1 - 1)
+          dw[1] = __fmul2_rn(__ffma2_rn(sp[0], m1, sp[2]), A2);   // A (sp2 - sp0)
+          dw[2] = __ffma2_rn(__fadd2_rn(sp[1], sp[2]), nA2, A2);  // A (1 - sp1 - sp2)
+        } else {
+          float2 xs[3];
+          xs[0] = __fadd2_rn(__fadd2_rn(sp[0], sp[1]), m1);
+          xs[1] = __ffma2_rn(sp[0], m1, sp[2]);
+          xs[2] = __ffma2_rn(__fadd2_rn(sp[1], sp[2]), m1, one2);
+#pragma unroll
+          for (int cc = 0; cc < 3; ++cc)
+            dw[cc] = __fmul2_rn(xs[cc], __ffma2_rn(B2, __fmul2_rn(xs[cc], xs[cc]), A2));
+        }
+        float2 d = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc) d = __ffma2_rn(__fadd2_rn(ryy[cc], ncy[p][cc]), dw[cc], d);
+        float2 nr = __ffma2_rn(d, m1, make_float2(dl[2 * p], dl[2 * p + 1]));
+        if (masked) {
+          const int cl = 4 * lane + 2 * p;
+          const bool rok = (int64_t)I * TILE + rl < n;
+          const bool ok0 = rok && ((int64_t)J * TILE + cl < n) && (I != J || rl < cl);
+          const bool ok1 = rok && ((int64_t)J * TILE + cl + 1 < n) && (I != J || rl < cl + 1);
+          nr.x = ok0 ? nr.x : 0.f;
+          nr.y = ok1 ? nr.y : 0.f;
+        }
+        S2 = __ffma2_rn(nr, nr, S2);
+        if (GRAD) {
+#pragma unroll
+          for (int cc = 0; cc < 3; ++cc) {
+            rn[cc] = __ffma2_rn(nr, dw[cc], rn[cc]);
+            cacc[p][cc] = __ffma2_rn(nr, dw[cc], cacc[p][cc]);
+          }
+        }
+      }
+#pragma unroll
+      for (int a = 0; a < 3; ++a) racc8[a][q] = -(rn[a].x + rn[a].y);
+    }
+    // this warp is done with the stage; the last warp to finish refills it
+    __syncwarp();
+    if (lane == 0) {
+      __threadfence_block();
+      if (atomicAdd(&s_done[s], 1u) == WARPS - 1) {
+        s_done[s] = 0;
+        const int cn = c + S;
+        if (cn < nchunks) {
+          int i2 = I, j2 = J;
+          for (int k2 = c / 2; k2 < cn / 2; ++k2) tile_next(i2, j2, Q.tiles);
+          __threadfence_block();
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          fused3_issue<DT>(Q, s_stage, bar_full, S, t_begin, ntiles, cn, i2, j2);
+        }
+      }
+    }
+    if (GRAD) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) rowacc[h][a] += reduce8(racc8[a], lane);
+    }
+    if (h == 1) {
+      const float y = (S2.x + S2.y) - Scomp;  // fold the tile's FP32 partial (Kahan)
+      const float tsum = Ssum + y;
+      Scomp = (tsum - Ssum) - y;
+      Ssum = tsum;
+      S2 = make_float2(0.f, 0.f);
+      if (GRAD) {
+        const int64_t tcur = t_begin + (c >> 1);
+        if (Q.part && lane < 8) {  // deterministic: this tile's row sums
+          const int rl = warp * 8 + rev3(lane);
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            if (GINI_IDX_OK(Q.err, (2 * tcur * TILE + rl + CHUNK_ROWS) * 3 + a,
+                            2 * ntiles * TILE * 3)) {
+              Q.part[(2 * tcur * TILE + rl) * 3 + a] = rowacc[0][a];
+              Q.part[(2 * tcur * TILE + rl + CHUNK_ROWS) * 3 + a] = rowacc[1][a];
+            }
+            rowacc[0][a] = rowacc[1][a] = 0.f;
+          }
+        }
+        float* cw = s_colw[(c >> 1) & 1][warp];
+#pragma unroll
+        for (int p = 0; p < 2; ++p)
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            cw[(4 * lane + 2 * p) * 3 + a] = cacc[p][a].x;
+            cw[(4 * lane + 2 * p + 1) * 3 + a] = cacc[p][a].y;
+          }
+        named_bar_sync(FUSED_THREADS);
+        for (int e = threadIdx.x; e < TILE * 3; e += FUSED_THREADS) {
+          float v = 0.f;
+#pragma unroll
+          for (int w = 0; w < WARPS; ++w) v += s_colw[(c >> 1) & 1][w][e];
+          const int64_t gj = (int64_t)J * TILE + e / 3;
+          if (Q.part) {
+            if (GINI_IDX_OK(Q.err, (2 * tcur + 1) * TILE * 3 + e, 2 * ntiles * TILE * 3))
+              Q.part[(2 * tcur + 1) * TILE * 3 + e] = v;
+          } else if (gj < n) {
+            atomicAdd(Q.h + gj * 3 + e % 3, v);
+          }
+        }
+      }
+    }
+  }
+  if (GRAD && !Q.part && curI >= 0 && lane < 8) {
+    const int64_t gi = (int64_t)curI * TILE + warp * 8 + rev3(lane);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (gi < n) atomicAdd(Q.h + gi * 3 + a, rowacc[0][a]);
+      if (gi + CHUNK_ROWS < n) atomicAdd(Q.h + (gi + CHUNK_ROWS) * 3 + a, rowacc[1][a]);
+    }
+  }
+  // Copies still in flight must land before this CTA's shared memory can be
+  // released: normally every issued chunk has been waited for already.
+  if (threadIdx.x == 0)
+    for (int c = (nchunks > S ? nchunks - S : 0); c < nchunks; ++c)
+      mbar_wait_bounded(&bar_full[c % S], (c / S) & 1, nullptr);
+  block_store_stress((double)Ssum - (double)Scomp, Q.stress);
+}
+
 // ------------------------------------------------------ update, finalize ---
 
 // Y <- Y - scale * h (scale = eta * 2 / sum_delta2; for k = 2 the gradient is
 // c2 * h_i * (1, -1)), then refresh the point pairs and clear h.
 template <int K>
 __global__ void k_update(float* __restrict__ Y, int64_t n, float2* __restrict__ P,
-                         float* __restrict__ h, float scale, float c2, bool scalar2,
-                         unsigned* err) {
+                         float4* __restrict__ Y4, float* __restrict__ h, float scale, float c2,
+                         bool scalar2, unsigned* err) {
   constexpr int NP = K * (K - 1) / 2;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   bool bad = false;
@@ -1092,6 +1409,7 @@ __global__ void k_update(float* __restrict__ Y, int64_t n, float2* __restrict__ 
     for (int a = 0; a < K; ++a)
 #pragma unroll
       for (int b = a + 1; b < K; ++b) P[i * NP + (p++)] = point_pair(y[a], y[b]);
+    if (K == 3 && Y4) Y4[i] = make_float4(y[0], y[1], y[K - 1], 0.f);
   }
   if (__any_sync(FULL_MASK, bad) && (threadIdx.x & 31) == 0) raise_error(err, ERR_NONFINITE);
 }
@@ -1169,6 +1487,7 @@ __global__ void __launch_bounds__(8 * TILE) k_det_reduce(const float* __restrict
 
 struct IterWs {
   float2* P;
+  float4* Y4;    // k = 3 only
   float* h;
   double* acc;   // nacc x STRESS_SLOTS stress slots
   float* part;   // deterministic mode: per-tile gradient partials, else null
@@ -1185,9 +1504,10 @@ extern "C" void gini_set_cuda_error(cudaError_t e);
 extern "C" int gini_get_deterministic(void);
 
 // Workspace of the iteration ops: header | nacc x STRESS_SLOTS doubles | point
-// pairs | h | (deterministic mode) per-tile gradient partials.  Point pairs are
-// stored for ceil(n / B) * B points (whole tiles, the padding zero-filled) so
-// that bulk copies of a tile's points never leave the array.
+// pairs | h | (k = 3) padded coordinates | (deterministic mode) per-tile
+// gradient partials.  Point pairs and padded coordinates are stored for
+// ceil(n / B) * B points (whole tiles, the padding zero-filled) so that bulk
+// copies of a tile's points never leave the arrays.
 static int64_t padded_points(int64_t n) { return tiles_1d(n) * TILE; }
 
 static size_t part_floats(int64_t n, int k) {
@@ -1200,6 +1520,7 @@ extern "C" size_t gini_iter_ws_bytes(int64_t n, int k, int nacc, int det) {
   return WS_HEADER + align256(sizeof(double) * (size_t)nacc * STRESS_SLOTS) +
          align256(sizeof(float2) * (size_t)padded_points(n) * np) +
          align256(sizeof(float) * (size_t)n * k) +
+         (k == 3 ? align256(sizeof(float4) * (size_t)padded_points(n)) : 0) +
          (det ? align256(sizeof(float) * part_floats(n, k)) : 0);
 }
 
@@ -1214,6 +1535,11 @@ static IterWs carve(void* ws, int64_t n, int k, int nacc, bool det) {
   p += align256(sizeof(float2) * (size_t)padded_points(n) * (k * (k - 1) / 2));
   w.h = reinterpret_cast<float*>(p);
   p += align256(sizeof(float) * (size_t)n * k);
+  w.Y4 = nullptr;
+  if (k == 3) {
+    w.Y4 = reinterpret_cast<float4*>(p);
+    p += align256(sizeof(float4) * (size_t)padded_points(n));
+  }
   w.part = det ? reinterpret_cast<float*>(p) : nullptr;
   return w;
 }
@@ -1261,41 +1587,44 @@ static int check_common(int64_t n, int k, double nu, const void* delta, int layo
 }
 
 template <int K>
-static void launch_prep(const float* Y, int64_t n, float2* P, unsigned* err, cudaStream_t s) {
+static void launch_prep(const float* Y, int64_t n, float2* P, float4* Y4, unsigned* err,
+                        cudaStream_t s) {
   const int64_t npad = padded_points(n);
   gini_count_launch(1);
-  k_prep<K><<<(unsigned)((npad + 255) / 256), 256, 0, s>>>(Y, n, npad, P, err);
+  k_prep<K><<<(unsigned)((npad + 255) / 256), 256, 0, s>>>(Y, n, npad, P, Y4, err);
 }
 
-static void prep(int k, const float* Y, int64_t n, float2* P, unsigned* err, cudaStream_t s) {
+static void prep(int k, const float* Y, int64_t n, float2* P, float4* Y4, unsigned* err,
+                 cudaStream_t s) {
   switch (k) {
-    case 2: launch_prep<2>(Y, n, P, err, s); break;
-    case 3: launch_prep<3>(Y, n, P, err, s); break;
-    case 4: launch_prep<4>(Y, n, P, err, s); break;
-    case 5: launch_prep<5>(Y, n, P, err, s); break;
-    case 6: launch_prep<6>(Y, n, P, err, s); break;
-    case 7: launch_prep<7>(Y, n, P, err, s); break;
-    default: launch_prep<8>(Y, n, P, err, s); break;
+    case 2: launch_prep<2>(Y, n, P, Y4, err, s); break;
+    case 3: launch_prep<3>(Y, n, P, Y4, err, s); break;
+    case 4: launch_prep<4>(Y, n, P, Y4, err, s); break;
+    case 5: launch_prep<5>(Y, n, P, Y4, err, s); break;
+    case 6: launch_prep<6>(Y, n, P, Y4, err, s); break;
+    case 7: launch_prep<7>(Y, n, P, Y4, err, s); break;
+    default: launch_prep<8>(Y, n, P, Y4, err, s); break;
   }
 }
 
 template <int K>
-static void launch_update(float* Y, int64_t n, float2* P, float* h, float scale, float c2,
-                          bool scalar2, unsigned* err, cudaStream_t s) {
+static void launch_update(float* Y, int64_t n, float2* P, float4* Y4, float* h, float scale,
+                          float c2, bool scalar2, unsigned* err, cudaStream_t s) {
   gini_count_launch(1);
-  k_update<K><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(Y, n, P, h, scale, c2, scalar2, err);
+  k_update<K><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(Y, n, P, Y4, h, scale, c2, scalar2,
+                                                          err);
 }
 
-static void update(int k, float* Y, int64_t n, float2* P, float* h, float scale, float c2,
-                   bool scalar2, unsigned* err, cudaStream_t s) {
+static void update(int k, float* Y, int64_t n, float2* P, float4* Y4, float* h, float scale,
+                   float c2, bool scalar2, unsigned* err, cudaStream_t s) {
   switch (k) {
-    case 2: launch_update<2>(Y, n, P, h, scale, c2, scalar2, err, s); break;
-    case 3: launch_update<3>(Y, n, P, h, scale, c2, scalar2, err, s); break;
-    case 4: launch_update<4>(Y, n, P, h, scale, c2, scalar2, err, s); break;
-    case 5: launch_update<5>(Y, n, P, h, scale, c2, scalar2, err, s); break;
-    case 6: launch_update<6>(Y, n, P, h, scale, c2, scalar2, err, s); break;
-    case 7: launch_update<7>(Y, n, P, h, scale, c2, scalar2, err, s); break;
-    default: launch_update<8>(Y, n, P, h, scale, c2, scalar2, err, s); break;
+    case 2: launch_update<2>(Y, n, P, Y4, h, scale, c2, scalar2, err, s); break;
+    case 3: launch_update<3>(Y, n, P, Y4, h, scale, c2, scalar2, err, s); break;
+    case 4: launch_update<4>(Y, n, P, Y4, h, scale, c2, scalar2, err, s); break;
+    case 5: launch_update<5>(Y, n, P, Y4, h, scale, c2, scalar2, err, s); break;
+    case 6: launch_update<6>(Y, n, P, Y4, h, scale, c2, scalar2, err, s); break;
+    case 7: launch_update<7>(Y, n, P, Y4, h, scale, c2, scalar2, err, s); break;
+    default: launch_update<8>(Y, n, P, Y4, h, scale, c2, scalar2, err, s); break;
   }
 }
 
@@ -1334,6 +1663,21 @@ static void launch_fusedk(unsigned g, const IterParams& Q, int64_t ntiles, cudaS
   k_fusedk<K, DT, GRAD, GK, AFF><<<g, FUSED_THREADS, smem, s>>>(Q, ntiles);
 }
 
+template <int DT, bool GRAD, bool AFF>
+static void launch_fused3(const IterParams& Q, int64_t ntiles, cudaStream_t s) {
+  using C = Pipe3Cfg<DT>;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_fused3<DT, GRAD, AFF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         C::smem);
+    attr = true;
+  }
+  const int64_t cap = std::min<int64_t>((int64_t)sm_count() * 2, STRESS_SLOTS);
+  const unsigned g = (unsigned)(ntiles < cap ? ntiles : cap);
+  gini_count_launch(1);
+  k_fused3<DT, GRAD, AFF><<<g, FUSED_THREADS, C::smem, s>>>(Q, ntiles);
+}
+
 template <int DT, bool GRAD>
 static void launch_fused_dt(int k, const IterParams& Q, cudaStream_t s) {
   const int64_t ntiles = Q.tiles * (Q.tiles + 1) / 2;
@@ -1347,9 +1691,9 @@ static void launch_fused_dt(int k, const IterParams& Q, cudaStream_t s) {
           // the table's cubic term B = (4 T(1) - 8 T(1/2)) / 3 is exactly zero
           // when T(1) = 2 T(1/2) in FP32 (nu = 2 or 3)
           if (Q.tab.w[4] == 2.f * Q.tab.w[3])
-            launch_fusedk<3, DT, GRAD, true, true>(g, Q, ntiles, s);
+            launch_fused3<DT, GRAD, true>(Q, ntiles, s);
           else
-            launch_fusedk<3, DT, GRAD, true>(g, Q, ntiles, s);
+            launch_fused3<DT, GRAD, false>(Q, ntiles, s);
         } else
           launch_fusedk<3, DT, GRAD>(g, Q, ntiles, s);
         return;
@@ -1424,6 +1768,7 @@ static IterParams make_params(int64_t n, int k, double nu, const float* Y, const
   Q.n = n;
   Q.P = w.P;
   Q.Y = Y;
+  Q.Y4 = w.Y4;
   Q.delta = delta;
   Q.ldd = ldd;
   Q.col_scale = col_scale;
@@ -1460,7 +1805,7 @@ extern "C" int gini_stress_grad_ex(const float* Y_dev, int64_t n, int k, double 
   cudaError_t e = cudaMemsetAsync(w.acc, 0, sizeof(double) * STRESS_SLOTS, s);
   if (e == cudaSuccess && grad_dev) e = cudaMemsetAsync(w.h, 0, sizeof(float) * n * k, s);
   if (e != cudaSuccess) { gini_set_cuda_error(e); return GINI_ECUDA; }
-  prep(k, Y_dev, n, w.P, w.err, s);
+  prep(k, Y_dev, n, w.P, w.Y4, w.err, s);
   one_pass(k, layout, dtype, grad_dev != nullptr, Q, s);
   gini_count_launch(grad_dev ? 2 : 1);
   k_finalize_stress<<<1, 32, 0, s>>>(w.acc, 1, 1.0 / norm, nullptr, stress_dev);  // one warp
@@ -1508,7 +1853,7 @@ extern "C" int gini_mds_fit(const gini_fit_args* a, void* ws, size_t ws_bytes, v
   cudaError_t e = cudaMemsetAsync(w.acc, 0, sizeof(double) * (size_t)(T + 1) * STRESS_SLOTS, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(w.h, 0, sizeof(float) * n * k, s);
   if (e != cudaSuccess) { gini_set_cuda_error(e); return GINI_ECUDA; }
-  prep(k, a->Y_dev, n, w.P, w.err, s);
+  prep(k, a->Y_dev, n, w.P, w.Y4, w.err, s);
   const float scale = (float)(a->eta * 2.0 / a->sum_delta2);
   const int polish_from = T - (a->polish_iters < T ? a->polish_iters : T);
   for (int t = 0; t < T; ++t) {
@@ -1516,7 +1861,7 @@ extern "C" int gini_mds_fit(const gini_fit_args* a, void* ws, size_t ws_bytes, v
     if (dt == GINI_BF16X2 && a->layout == GINI_LAYOUT_TILED && t < polish_from) dt = GINI_BF16;
     Q.stress = w.acc + (size_t)t * STRESS_SLOTS;
     one_pass(k, a->layout, dt, true, Q, s);
-    update(k, a->Y_dev, n, w.P, w.h, scale, Q.tab.c2, sc2, w.err, s);
+    update(k, a->Y_dev, n, w.P, w.Y4, w.h, scale, Q.tab.c2, sc2, w.err, s);
   }
   Q.stress = w.acc + (size_t)T * STRESS_SLOTS;
   one_pass(k, a->layout, a->dtype, false, Q, s);
