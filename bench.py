@@ -168,13 +168,16 @@ def _peaks():
     return 6800.0, "fallback"
 
 
-def _profile_traffic():
-    """DRAM bytes per launch of the Delta-build kernel from the committed ncu
-    summary (scaled to this workload), or None."""
+def _profile_traffic(workload):
+    """DRAM bytes per launch of the Delta-build and iteration kernels from the
+    committed ncu summary, when it was captured on this workload; else {}
+    (the figures then go out as null)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(p):
         with open(p) as f:
-            return json.load(f)
+            t = json.load(f)
+        if str(t.get("workload", "")).split(" ")[0] == workload:
+            return t
     return {}
 
 
@@ -261,7 +264,7 @@ def run_ours(args, rank, local, world):
     max_mhz = clocks.get("sm_max_mhz") or 2070.0
     alu_peak = sms * 64 * max_mhz * 1e6
     achieved_ops = P * ops_per_pair / b_s
-    traffic = _profile_traffic()
+    traffic = _profile_traffic(args.workload)
 
     # iteration phase: algorithmic bytes = P pairs x stored bytes per pair
     # (BF16 hi 2, hi + lo 4, F32 4), averaged over the schedule.

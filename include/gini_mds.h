@@ -242,7 +242,7 @@ int gini_stress_grad(const float* Y_dev, int64_t n, int k, double nu, const void
  * workspace: the scratch space is a fixed 8 MiB array inside the library, which
  * every GPU that loads the library holds until the process exits.
  *   - Sizes whose gini_workspace_size(GINI_OP_STRESS, n, 0, k, 0) exceeds 8 MiB
- *     (about 520,000 points at k = 2, 230,000 at k = 3) return GINI_ENOMEM
+ *     (about 520,000 points at k = 2, 160,000 at k = 3) return GINI_ENOMEM
  *     before anything is enqueued.
  *   - The first call on a device looks up the array's device address with that
  *     device current; make that first call before any stream capture.

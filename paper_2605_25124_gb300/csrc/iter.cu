@@ -720,9 +720,8 @@ struct FusedKSmem {
   float colh[TILE][K];
 };
 
-// GK: Gini metric and Kruskal loss only (the other branches compiled out, so the
-// unrolled body stays small enough for the instruction cache).
-template <int K, int DT, bool GRAD, bool GK, bool AFF = false>
+// (k = 3 with the Gini metric and Kruskal's loss runs in k_fused3 below.)
+template <int K, int DT, bool GRAD>
 __global__ void __launch_bounds__(FUSED_THREADS, 2) k_fusedk(const IterParams Q, int64_t ntiles) {
   constexpr int NP = K * (K - 1) / 2;
   extern __shared__ __align__(16) unsigned char s_raw[];
@@ -784,11 +783,11 @@ __global__ void __launch_bounds__(FUSED_THREADS, 2) k_fusedk(const IterParams Q,
       const int64_t gi = i0 + rl;
       const bool ok = gi < Q.n && j0 + cl < Q.n && (I != J || rl < cl);
       float dw[K];
-      const float d = (!GK && Q.metric == GINI_METRIC_EUCLID)
+      const float d = (Q.metric == GINI_METRIC_EUCLID)
                           ? pair_euclid<K>(s_y[0][rl], s_y[1][cl], dw)
                           : pair_k<K>(s_y[0][rl], s_y[1][cl], s_p[0][rl], s_p[1][cl], s_w, dw);
       float sterm, gw;
-      loss_terms(GK ? GINI_LOSS_KRUSKAL : Q.loss, d, dl[c], sterm, gw);
+      loss_terms(Q.loss, d, dl[c], sterm, gw);
       sterm = ok ? sterm : 0.f;
       gw = ok ? gw : 0.f;
       S += sterm;
@@ -807,10 +806,10 @@ __global__ void __launch_bounds__(FUSED_THREADS, 2) k_fusedk(const IterParams Q,
       const int64_t gi = i0 + rl;
       const bool ok = gi < Q.n && j0 + cl < Q.n && (I != J || rl < cl);
       float dw[K];
-      const float d = (!GK && Q.metric == GINI_METRIC_EUCLID) ? pair_euclid<K>(ry, cy, dw)
+      const float d = (Q.metric == GINI_METRIC_EUCLID) ? pair_euclid<K>(ry, cy, dw)
                                                               : pair_k<K>(ry, cy, rp, cpp, s_w, dw);
       float sterm, gw;
-      loss_terms(GK ? GINI_LOSS_KRUSKAL : Q.loss, d, dl[c], sterm, gw);
+      loss_terms(Q.loss, d, dl[c], sterm, gw);
       sterm = ok ? sterm : 0.f;
       gw = ok ? gw : 0.f;
       S += sterm;
@@ -834,125 +833,6 @@ __global__ void __launch_bounds__(FUSED_THREADS, 2) k_fusedk(const IterParams Q,
 #pragma unroll
         for (int q = 0; q < NP; ++q) cp[c][q] = s_p[1][4 * lane + c][q];
       }
-      if constexpr (K == 3 && GK) {
-        // k = 3, Gini metric, Kruskal loss: two columns per packed f32x2
-        // instruction.  For a rank comparison with exact sign sigma,
-        // sp = sat(a 2^126 + 1/2) = (sigma + 1) / 2 in one saturating FMA
-        // (a = fma(dh, 2^88, dl') on the scaled point pairs, point_pair), and
-        // the midrank offsets x_c = R_c - 2 are affine in the three sp.  The
-        // residual is carried negated, nr = delta - d: S += nr^2, and the row
-        // and column sums of dd/dy weighted by r both collect nr * dw (the row
-        // sum negated when it is flushed, the column sum needs -r dw).
-        const float t1 = s_w[4], th = s_w[3];
-        const float A = (8.f * th - t1) * (1.f / 3.f), B = (4.f * t1 - 8.f * th) * (1.f / 3.f);
-        const float2 A2 = make_float2(A, A), B2 = make_float2(B, B), nA2 = make_float2(-A, -A);
-        const float2 khi = make_float2(SIGN_HI, SIGN_HI);
-        const float2 m1 = make_float2(-1.f, -1.f), one2 = make_float2(1.f, 1.f);
-        float2 ncy[2][3], nch[2][3], ncl[2][3], cacc[2][3];
-#pragma unroll
-        for (int p = 0; p < 2; ++p)
-#pragma unroll
-          for (int a = 0; a < 3; ++a) {
-            ncy[p][a] = make_float2(-cy[2 * p][a], -cy[2 * p + 1][a]);
-            nch[p][a] = make_float2(-cp[2 * p][a].x, -cp[2 * p + 1][a].x);
-            ncl[p][a] = make_float2(-cp[2 * p][a].y, -cp[2 * p + 1][a].y);
-            cacc[p][a] = make_float2(0.f, 0.f);
-          }
-        const bool masked = (I == J) || (i0 + TILE > Q.n) || (j0 + TILE > Q.n);
-        float2 S2 = make_float2(0.f, 0.f);
-        for (int rb = 0; rb < 16; rb += 8) {
-          float racc8[3][8];
-#pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            const int rl = warp * 16 + rb + q;
-            float dl[4];
-            load4<DT>(Q, tbase + (int64_t)rl * TILE + 4 * lane, dl, sc);
-            float2 ryy[3], rph[3], rpl[3], rn[3];
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-              const float yv = s_y[0][rl][a];
-              const float2 pv = s_p[0][rl][a];
-              ryy[a] = make_float2(yv, yv);
-              rph[a] = make_float2(pv.x, pv.x);
-              rpl[a] = make_float2(pv.y, pv.y);
-              rn[a] = make_float2(0.f, 0.f);
-            }
-#pragma unroll
-            for (int p = 0; p < 2; ++p) {
-              float2 sp[3];
-#pragma unroll
-              for (int qq = 0; qq < 3; ++qq) {
-                const float2 dh = __fadd2_rn(rph[qq], nch[p][qq]);
-                const float2 dlo = __fadd2_rn(rpl[qq], ncl[p][qq]);
-                const float2 a = __ffma2_rn(dh, khi, dlo);  // dlo scaled by 2^24
-                sp[qq] = make_float2(__saturatef(fmaf(a.x, SIGN_SAT, 0.5f)),
-                                     __saturatef(fmaf(a.y, SIGN_SAT, 0.5f)));
-              }
-              float2 dw[3];
-              if constexpr (AFF) {
-                // B = 0 (a table affine in the rank: nu = 2 or 3): dw_c = A x_c,
-                // formed from the sp in one FMA each.  x_c is in {0, +-1/2, +-1},
-                // so A x_c is exact and these are the general form's bits.
-                dw[0] = __ffma2_rn(__fadd2_rn(sp[0], sp[1]), A2, nA2);  // A (sp0 + sp1 - 1)
-                dw[1] = __fmul2_rn(__ffma2_rn(sp[0], m1, sp[2]), A2);   // A (sp2 - sp0)
-                dw[2] = __ffma2_rn(__fadd2_rn(sp[1], sp[2]), nA2, A2);  // A (1 - sp1 - sp2)
-              } else {
-                float2 xs[3];
-                xs[0] = __fadd2_rn(__fadd2_rn(sp[0], sp[1]), m1);  // (s01 + s02) / 2
-                xs[1] = __ffma2_rn(sp[0], m1, sp[2]);              // (s12 - s01) / 2
-                xs[2] = __ffma2_rn(__fadd2_rn(sp[1], sp[2]), m1, one2);  // -(s02 + s12) / 2
-#pragma unroll
-                for (int c = 0; c < 3; ++c)
-                  dw[c] = __fmul2_rn(xs[c], __ffma2_rn(B2, __fmul2_rn(xs[c], xs[c]), A2));
-              }
-              float2 d = make_float2(0.f, 0.f);
-#pragma unroll
-              for (int c = 0; c < 3; ++c) d = __ffma2_rn(__fadd2_rn(ryy[c], ncy[p][c]), dw[c], d);
-              float2 nr = __ffma2_rn(d, m1, make_float2(dl[2 * p], dl[2 * p + 1]));
-              if (masked) {
-                const int cl = 4 * lane + 2 * p;
-                const bool rok = i0 + rl < Q.n;
-                const bool ok0 = rok && (j0 + cl < Q.n) && (I != J || rl < cl);
-                const bool ok1 = rok && (j0 + cl + 1 < Q.n) && (I != J || rl < cl + 1);
-                nr.x = ok0 ? nr.x : 0.f;
-                nr.y = ok1 ? nr.y : 0.f;
-              }
-              S2 = __ffma2_rn(nr, nr, S2);
-#pragma unroll
-              for (int c = 0; c < 3; ++c) {
-                rn[c] = __ffma2_rn(nr, dw[c], rn[c]);
-                cacc[p][c] = __ffma2_rn(nr, dw[c], cacc[p][c]);
-              }
-            }
-#pragma unroll
-            for (int a = 0; a < 3; ++a) racc8[a][q] = -(rn[a].x + rn[a].y);
-          }
-          if (GRAD) {
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-              const float v = reduce8(racc8[a], lane);
-              const int rl = warp * 16 + rb + rev3(lane & 7);
-              const int64_t gi = i0 + rl;
-              if (lane < 8) {
-                if (Q.part) {
-                  if (GINI_IDX_OK(Q.err, (2 * t * TILE + rl) * K + a, 2 * ntiles * TILE * K))
-                    Q.part[(2 * t * TILE + rl) * K + a] = v;
-                } else if (gi < Q.n) {
-                  atomicAdd(Q.h + gi * K + a, v);
-                }
-              }
-            }
-          }
-        }
-        S += S2.x + S2.y;
-#pragma unroll
-        for (int p = 0; p < 2; ++p)
-#pragma unroll
-          for (int a = 0; a < 3; ++a) {
-            colacc[2 * p][a] = cacc[p][a].x;
-            colacc[2 * p + 1][a] = cacc[p][a].y;
-          }
-      } else
       for (int rb = 0; rb < 16; rb += 8) {
         float racc8[K][8];
 #pragma unroll
@@ -1651,16 +1531,16 @@ static void full_k(int k, const IterParams& Q, cudaStream_t s) {
   }
 }
 
-template <int K, int DT, bool GRAD, bool GK = false, bool AFF = false>
+template <int K, int DT, bool GRAD>
 static void launch_fusedk(unsigned g, const IterParams& Q, int64_t ntiles, cudaStream_t s) {
   // deterministic mode: per-warp column sums after the staged points
   const size_t smem = sizeof(FusedKSmem<K>) +
                       (GRAD && Q.part ? sizeof(float) * (FUSED_THREADS / 32) * TILE * K : 0);
   if (smem + 1024 > 48 * 1024)  // plus the kernel's static shared memory
-    cudaFuncSetAttribute(k_fusedk<K, DT, GRAD, GK, AFF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_fusedk<K, DT, GRAD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
   gini_count_launch(1);
-  k_fusedk<K, DT, GRAD, GK, AFF><<<g, FUSED_THREADS, smem, s>>>(Q, ntiles);
+  k_fusedk<K, DT, GRAD><<<g, FUSED_THREADS, smem, s>>>(Q, ntiles);
 }
 
 template <int DT, bool GRAD, bool AFF>

@@ -8,7 +8,7 @@
 namespace gini {
 
 // Largest scratch the variant offers: gini_workspace_size(GINI_OP_STRESS, n, 0,
-// k, 0) must not exceed it (about 520,000 points at k = 2, 230,000 at k = 3).
+// k, 0) must not exceed it (about 520,000 points at k = 2, 160,000 at k = 3).
 constexpr size_t NOALLOC_SCRATCH_BYTES = (size_t)8 << 20;
 
 // One copy per device that loads the library, held until the process exits.
