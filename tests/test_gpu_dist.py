@@ -11,7 +11,7 @@ import torch
 
 from oracle import gini_oracle as orc
 from paper_2605_25124_gb300 import workloads as wl
-from util import ENTRY_TOL, NORM_TOL, fro_rel, rel_err, untile
+from util import ENTRY_TOL, NORM_TOL, fro_rel, rel_err, tiled_flat_index, untile
 
 pytestmark = pytest.mark.gpu
 
@@ -135,6 +135,65 @@ def test_delta_full_size_image_workload_sampled(G):
     for q in range(3):
         d = mats[q].data.double()
         assert sd2[q].item() == pytest.approx(0.5 * float((d * d).sum()), rel=1e-9)
+
+
+def _e4m3_decode(q):
+    """e4m3 bytes -> float64 (sign, 4-bit exponent with bias 7, 3-bit mantissa)."""
+    q = np.asarray(q, dtype=np.uint8)
+    s = np.where(q & 0x80, -1.0, 1.0)
+    e = ((q >> 3) & 0xF).astype(np.float64)
+    m = (q & 7).astype(np.float64)
+    return s * np.where(e == 0, m / 8 * 2.0 ** -6, (1 + m / 8) * 2.0 ** (e - 7))
+
+
+def test_delta_storage_forms_at_the_image_configuration(G):
+    """n = 2000, p = 784, nu in {1.5, 2, 3}: the tiled BF16, BF16 hi+lo and
+    FP8 e4m3 (per-column scale) outputs of gini_dist against the FP64 oracle on
+    2,000 sampled pairs and one whole row, each within its storage bound:
+    bf16 round-to-nearest 2^-8 relative, hi+lo 2^-16, e4m3 half an ulp of a
+    3-bit mantissa (2^-4 relative) or 2^-10 of the column scale near zero; plus
+    the FP32 build's own 1e-5.  The worst errors are printed for the record."""
+    w = wl.WORKLOADS["image-n2000-p784"]
+    n, nus = w["n"], [float(v) for v in w["nu"]]
+    X = wl.make_X("image-n2000-p784")
+    rng = np.random.default_rng(2024)
+    I = rng.integers(0, n, 2000)
+    J = rng.integers(0, n, 2000)
+    keep = I != J
+    I, J = np.minimum(I[keep], J[keep]), np.maximum(I[keep], J[keep])
+    row = 777
+    I = np.concatenate([I, np.full(n - 1 - row, row), np.arange(row)])
+    J = np.concatenate([J, np.arange(row + 1, n), np.full(row, row)])
+    ref = orc.delta_pairs(X, nus, I, J)  # (pairs, nu)
+    idx = tiled_flat_index(I, J, n)
+    plane = -(-n // 128) * (-(-n // 128) + 1) // 2 * 128 * 128
+    Xd = torch.from_numpy(X).cuda()
+    worst = {}
+    for dtype in ("bf16", "bf16x2", "fp8"):
+        mats, _ = G.gini_dist(Xd, nus, layout="tiled", dtype=dtype)
+        for q in range(len(nus)):
+            r = ref[:, q]
+            if dtype == "fp8":
+                got = _e4m3_decode(mats[q].data.cpu().numpy()[idx])
+                sc = mats[q].col_scale.cpu().numpy().astype(np.float64)[J]
+                got = got * sc
+                err = np.abs(got - r)
+                bound = (2.0 ** -4 + 1e-5) * np.abs(r) + 2.0 ** -10 * sc + 1e-7
+                assert np.all(err <= bound), (q, float(np.max(err / bound)))
+                worst[(dtype, nus[q])] = float(np.max(err / np.abs(r).max()))
+            else:
+                bits = mats[q].data.view(torch.int16).cpu().numpy().astype(np.uint16)
+                hi = (bits[idx].astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+                got = hi
+                if dtype == "bf16x2":
+                    lo = (bits[plane + idx].astype(np.uint32) << 16).view(np.float32)
+                    got = hi + lo.astype(np.float64)
+                tol = (2.0 ** -8 if dtype == "bf16" else 2.0 ** -16) + 1e-5
+                e = rel_err(got, r, 1e-6 * np.abs(r).max())
+                assert e <= tol, (dtype, q, e)
+                worst[(dtype, nus[q])] = e
+    print("worst entry errors against the FP64 oracle:",
+          {f"{k[0]} nu={k[1]}": f"{v:.2e}" for k, v in worst.items()})
 
 
 def test_delta_nonfinite_reported(G):
