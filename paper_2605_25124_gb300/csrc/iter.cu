@@ -23,6 +23,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <atomic>
 
 #define GINI_FILE_ID 2  // site numbers of the debug index checks
 #include "common.cuh"
@@ -1435,17 +1436,31 @@ static PairTab make_tab(int k, double nu) {
   return T;
 }
 
+// Per-device caches: a process may drive several GPUs (one per thread).
+constexpr int MAX_DEVICES = 64;
+
 static int sm_count() {
-  static int cached = 0;
-  if (!cached) {
-    int dev = 0, v = 0;
-    if (cudaGetDevice(&dev) == cudaSuccess &&
-        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
-      cached = v;
-    else
-      return 148;
-  }
-  return cached;
+  static std::atomic<int> cached[MAX_DEVICES];
+  int dev = 0, v = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) return 148;
+  const int c = cached[dev].load(std::memory_order_relaxed);
+  if (c > 0) return c;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0)
+    return 148;
+  cached[dev].store(v, std::memory_order_relaxed);
+  return v;
+}
+
+// The dynamic shared-memory limit above 48 KB is an attribute of the kernel on
+// each device: set it once per device (setting it twice is harmless).
+template <typename Kern>
+static void smem_attr_once(Kern* fn, int bytes, std::atomic<unsigned long long>& done) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return;
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (done.load(std::memory_order_acquire) & bit) return;
+  cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  done.fetch_or(bit, std::memory_order_acq_rel);
 }
 
 static int check_common(int64_t n, int k, double nu, const void* delta, int layout, int dtype,
@@ -1546,12 +1561,8 @@ static void launch_fusedk(unsigned g, const IterParams& Q, int64_t ntiles, cudaS
 template <int DT, bool GRAD, bool AFF>
 static void launch_fused3(const IterParams& Q, int64_t ntiles, cudaStream_t s) {
   using C = Pipe3Cfg<DT>;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_fused3<DT, GRAD, AFF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         C::smem);
-    attr = true;
-  }
+  static std::atomic<unsigned long long> attr{0};
+  smem_attr_once(k_fused3<DT, GRAD, AFF>, C::smem, attr);
   const int64_t cap = std::min<int64_t>((int64_t)sm_count() * 2, STRESS_SLOTS);
   const unsigned g = (unsigned)(ntiles < cap ? ntiles : cap);
   gini_count_launch(1);
@@ -1587,14 +1598,16 @@ static void launch_fused_dt(int k, const IterParams& Q, cudaStream_t s) {
   switch (k) {
     case 2: {
       using C = PipeCfg<DT>;
-      static int per_sm = 0;  // resident CTAs per SM for this instance
+      static std::atomic<unsigned long long> attr{0};
+      smem_attr_once(k_fused2<DT, GRAD>, C::smem, attr);
+      static std::atomic<int> per_sm_cached{0};  // resident CTAs per SM (same on every GB300)
+      int per_sm = per_sm_cached.load(std::memory_order_relaxed);
       if (!per_sm) {
-        cudaFuncSetAttribute(k_fused2<DT, GRAD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             C::smem);
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused2<DT, GRAD>,
                                                           PIPE_THREADS, C::smem) != cudaSuccess ||
             per_sm < 1)
           per_sm = 1;
+        per_sm_cached.store(per_sm, std::memory_order_relaxed);
       }
       const int64_t cap2 = std::min<int64_t>((int64_t)sm_count() * per_sm, STRESS_SLOTS);
       const unsigned g2 = (unsigned)(ntiles < cap2 ? ntiles : cap2);
