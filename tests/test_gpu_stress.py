@@ -35,7 +35,7 @@ def _ref_delta(n, p, nu, seed):
 
 
 @pytest.mark.parametrize("dtype", ["full", "f32", "bf16", "bf16x2", "fp8"])
-@pytest.mark.parametrize("k,nu", [(2, 2.0), (2, 1.5), (3, 3.0), (4, 1.3), (8, 2.0)])
+@pytest.mark.parametrize("k,nu", [(2, 2.0), (2, 1.5), (3, 3.0), (3, 1.6), (4, 1.3), (8, 2.0)])
 def test_stress_grad_parity(G, dtype, k, nu):
     n = 300  # 3 tiles per edge, ragged tail
     X, D, sd2 = _ref_delta(n, 8, nu, seed=200 + k)
