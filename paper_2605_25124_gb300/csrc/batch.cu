@@ -214,7 +214,8 @@ k_batch_iter(const BatchParams B) {  // held to 128 registers: two 16-row CTAs p
           const float2 sp = make_float2(__saturatef(fmaf(a2.x, SIGN_SAT, 0.5f)),
                                         __saturatef(fmaf(a2.y, SIGN_SAT, 0.5f)));
           const float2 sig = __ffma2_rn(sp, k2, m1);  // 2 sp - 1
-          float2 rp = __ffma2_rn(nc2, __fmul2_rn(s2, sig), dv[p]);  // r' = delta - c2 |s|
+          // r' = delta - c2 |s|; s has the sign 0 or sigma, so |s| = s sigma (an AND)
+          float2 rp = __ffma2_rn(nc2, abs2_alu(s2), dv[p]);
           if (masked) {
             const int cl = 4 * lane + 2 * p;
             const bool rok = i0 + rl < n;
@@ -224,10 +225,9 @@ k_batch_iter(const BatchParams B) {  // held to 128 registers: two 16-row CTAs p
             rp.y = ok1 ? rp.y : 0.f;
           }
           S2 = __ffma2_rn(rp, rp, S2);
-          if (GRAD) {
-            const float2 tp = __fmul2_rn(rp, sig);  // -(r sign(s))
-            row2 = __fadd2_rn(row2, tp);
-            col2[p] = __fadd2_rn(col2[p], tp);
+          if (GRAD) {  // r' sigma = -(r sign(s))
+            row2 = __ffma2_rn(rp, sig, row2);
+            col2[p] = __ffma2_rn(rp, sig, col2[p]);
           }
         }
         rowv[q] = -(row2.x + row2.y);

@@ -124,15 +124,23 @@ __device__ __forceinline__ float2 two_diff(float a, float b) {
 // scaled part cannot overflow, and scaling by a power of two is exact and
 // keeps the order of the lo parts.  Two pairs' difference is then
 // dh = hi_i - hi_j and dl' = lo'_i - lo'_j = 2^24 fl(lo_i - lo_j):
-//   the value:     fma(dl', 2^-24, dh) = fl(dh + dl), as without the scaling;
 //   the exact sign: a = fma(dh, 2^88, dl') = 2^24 fl(dh 2^64 + dl) (dh decides
 //   when it is not zero, dl when it is), and every nonzero a has magnitude at
 //   least 2^-125, so sat(fma(a, 2^126, 1/2)) is exactly 0, 1/2 or 1 -- one
-//   FMA fewer than scaling a by 2^150 in two steps.
+//   FMA fewer than scaling a by 2^150 in two steps;
+//   the value:     s = fma(dl', 2^-24, dh) = fl(dh + dl), as without the
+//   scaling.  Its sign is 0 or the exact sign (rounding is monotone and -dh
+//   is a float, so it cannot cross it), so |s| = s sigma exactly.
 constexpr float LO_SCALE = 0x1p24f;
 constexpr float LO_UNSCALE = 0x1p-24f;
 constexpr float SIGN_HI = 0x1p88f;    // weight of dh in a
 constexpr float SIGN_SAT = 0x1p126f;  // takes every nonzero a to magnitude >= 2
+
+// |x| of both halves by clearing the sign bits (ALU pipe, not the FMA pipe).
+__device__ __forceinline__ float2 abs2_alu(float2 x) {
+  return make_float2(__uint_as_float(__float_as_uint(x.x) & 0x7fffffffu),
+                     __uint_as_float(__float_as_uint(x.y) & 0x7fffffffu));
+}
 
 __device__ __forceinline__ float2 point_pair(float a, float b) {
   const float2 t = two_diff(a, b);

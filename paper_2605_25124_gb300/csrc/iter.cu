@@ -464,7 +464,12 @@ __device__ __forceinline__ void load4_smem(const unsigned char* stage, int rr, i
 //   sigma: with the point pairs' lo parts scaled by 2^24 (point_pair),
 //   a = fma(dh, 2^88, dl') has the sign of u_i - u_j (dl cannot outweigh a
 //   non-zero dh; a = dl' exactly when dh = 0), and sat(a 2^126 + 1/2) maps it
-//   to exactly 0, 1/2 or 1 = (sigma + 1) / 2; s = fma(dl', 2^-24, dh).
+//   to exactly 0, 1/2 or 1 = (sigma + 1) / 2.
+//   |s|: s = fma(dl', 2^-24, dh) has the sign 0 or sigma, so |s| = s sigma;
+//   it is taken with an AND on the ALU pipe.  The lo parts matter here: near
+//   a converged fit the residual is orders of magnitude below delta, and
+//   dropping them (an error up to 2^-24 |u| in d) moved the gradient by 5e-4.
+//   t' = r' sigma is exact, so the row and column sums take it in one FMA.
 template <int DT, bool GRAD, bool MASKED>
 __device__ __forceinline__ void chunk_compute(const unsigned char* stage, int rbase, int lane,
                                               const float2 (&nuh)[2], const float2 (&nul)[2],
@@ -495,7 +500,7 @@ __device__ __forceinline__ void chunk_compute(const unsigned char* stage, int rb
       const float2 sp = make_float2(__saturatef(fmaf(a2.x, SIGN_SAT, 0.5f)),
                                     __saturatef(fmaf(a2.y, SIGN_SAT, 0.5f)));
       const float2 sig = __ffma2_rn(sp, k2, m1);  // 2 sp - 1
-      float2 rp = __ffma2_rn(nc2, __fmul2_rn(s2, sig), d2);  // r' = delta - c2 |s|
+      float2 rp = __ffma2_rn(nc2, abs2_alu(s2), d2);  // r' = delta - c2 |s|
       if (MASKED) {
         const int rl = rl0 + q, cl = 4 * lane + 2 * p;
         const bool ok0 = (gi0 + q < n) && (gj0 + 2 * p < n) && (!diag || rl < cl);
@@ -504,10 +509,9 @@ __device__ __forceinline__ void chunk_compute(const unsigned char* stage, int rb
         rp.y = ok1 ? rp.y : 0.f;
       }
       S2 = __ffma2_rn(rp, rp, S2);
-      if (GRAD) {
-        const float2 tp = __fmul2_rn(rp, sig);  // t' = -t
-        row2 = __fadd2_rn(row2, tp);
-        col2[p] = __fadd2_rn(col2[p], tp);
+      if (GRAD) {  // t' = r' sigma = -t
+        row2 = __ffma2_rn(rp, sig, row2);
+        col2[p] = __ffma2_rn(rp, sig, col2[p]);
       }
     }
     rowv[q] = -(row2.x + row2.y);
