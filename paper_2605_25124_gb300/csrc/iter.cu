@@ -388,17 +388,20 @@ struct PipeCfg {
   static constexpr int urow_off = planes * plane_bytes;
   static constexpr int ucol_off = urow_off + CHUNK_ROWS * 8;
   static constexpr int stage_bytes = ucol_off + TILE * 8;
-  // 104 KB of stages + ~8.5 KB static per CTA keeps two CTAs on an SM; the
-  // narrow forms (16-bit, 8-bit tiles) take ~54 KB so that three fit: there a
-  // chunk is half or a quarter of the FP32 bytes and the consumers' arithmetic
-  // per chunk is the same, so more warps, not more bytes in flight, is the gain
-  static constexpr int budget = (DT == GINI_BF16 || DT == GINI_FP8E4M3) ? 54 * 1024 : 104 * 1024;
+  // Three CTAs per SM for every form (the consumers are latency-bound, so
+  // more warps help):
+  //  - narrow forms (16-bit, 8-bit tiles): ~54 KB of stages + 8.5 KB static;
+  //  - wide forms (FP32, BF16 hi+lo): two 33.5 KB stages + 4.4 KB static, the
+  //    column slices single-buffered behind a second named barrier per tile.
+  // Bytes in flight per SM stay at six 32 KB chunks for the wide forms.
+  static constexpr bool wide = DT == GINI_F32 || DT == GINI_BF16X2;
+  static constexpr int budget = 54 * 1024;
   static constexpr int stages_raw = budget / stage_bytes;
-  static constexpr int stages = stages_raw > 8 ? 8 : stages_raw;
+  static constexpr int stages = wide ? 2 : (stages_raw > 8 ? 8 : stages_raw);
   static constexpr int smem = stages * stage_bytes;
-  // the narrow forms' three CTAs per SM, held to in registers too; 0 (no
-  // bound) for the wide forms, which their shared memory holds to two
-  static constexpr int min_ctas = budget < 64 * 1024 ? 3 : 0;
+  static constexpr int colbufs = wide ? 1 : 2;  // column-slice buffers
+  // held to in registers too: 65536 / (3 x 288) = 75 per thread (72 used)
+  static constexpr int min_ctas = 3;
 };
 
 // Sums a[0..7] over the 32 lanes; lane l returns the total of entry
@@ -526,7 +529,7 @@ k_fused2(const IterParams Q, int64_t ntiles) {
   extern __shared__ __align__(128) unsigned char s_stage[];
   __shared__ __align__(8) uint64_t bar_full[S];
   __shared__ __align__(8) uint64_t bar_empty[S];
-  __shared__ float s_colw[2][CONSUMER_WARPS][TILE];
+  __shared__ float s_colw[C::colbufs][CONSUMER_WARPS][TILE];
   __shared__ double s_red[CONSUMER_WARPS];
   __shared__ int s_abort;
 
@@ -679,14 +682,15 @@ k_fused2(const IterParams Q, int64_t ntiles) {
           rp[CHUNK_ROWS] = rowacc1;
           rowacc0 = rowacc1 = 0.f;
         }
-        float* cw = s_colw[(c >> 1) & 1][warp];
+        const int cb = (c >> 1) % C::colbufs;
+        float* cw = s_colw[cb][warp];
         *reinterpret_cast<float4*>(cw + 4 * lane) =
             make_float4(col2[0].x, col2[0].y, col2[1].x, col2[1].y);
         named_bar_sync(CONSUMER_WARPS * 32);
         if (threadIdx.x < TILE) {
           float v = 0.f;
 #pragma unroll
-          for (int w = 0; w < CONSUMER_WARPS; ++w) v += s_colw[(c >> 1) & 1][w][threadIdx.x];
+          for (int w = 0; w < CONSUMER_WARPS; ++w) v += s_colw[cb][w][threadIdx.x];
           const int64_t gj = (int64_t)J * TILE + threadIdx.x;
           if (Q.part) {
             if (GINI_IDX_OK(Q.err, (2 * tcur + 1) * TILE + threadIdx.x, 2 * ntiles * TILE))
@@ -695,6 +699,8 @@ k_fused2(const IterParams Q, int64_t ntiles) {
             atomicAdd(Q.h + gj, v);
           }
         }
+        // one slice buffer: every consumer has read it before the next tile writes
+        if (C::colbufs == 1) named_bar_sync(CONSUMER_WARPS * 32);
       }
     }
   }
