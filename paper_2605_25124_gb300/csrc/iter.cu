@@ -388,20 +388,21 @@ struct PipeCfg {
   static constexpr int urow_off = planes * plane_bytes;
   static constexpr int ucol_off = urow_off + CHUNK_ROWS * 8;
   static constexpr int stage_bytes = ucol_off + TILE * 8;
-  // Three CTAs per SM for every form (the consumers are latency-bound, so
-  // more warps help):
-  //  - narrow forms (16-bit, 8-bit tiles): ~54 KB of stages + 8.5 KB static;
-  //  - wide forms (FP32, BF16 hi+lo): two 33.5 KB stages + 4.4 KB static, the
-  //    column slices single-buffered behind a second named barrier per tile.
-  // Bytes in flight per SM stay at six 32 KB chunks for the wide forms.
+  // Several CTAs per SM (the consumers are latency-bound, so more warps help):
+  //  - narrow forms (16-bit, 8-bit tiles): four, with ~40 KB of stages + 8.5 KB
+  //    static each (BF16: two stages, FP8: four) at 56 registers;
+  //  - wide forms (FP32, BF16 hi+lo): three, with two 33.5 KB stages + 4.4 KB
+  //    static, the column slices single-buffered behind a second named
+  //    barrier per tile.  Bytes in flight per SM stay at six 32 KB chunks.
   static constexpr bool wide = DT == GINI_F32 || DT == GINI_BF16X2;
-  static constexpr int budget = 54 * 1024;
+  static constexpr int budget = 40 * 1024;
   static constexpr int stages_raw = budget / stage_bytes;
   static constexpr int stages = wide ? 2 : (stages_raw > 8 ? 8 : stages_raw);
   static constexpr int smem = stages * stage_bytes;
   static constexpr int colbufs = wide ? 1 : 2;  // column-slice buffers
-  // held to in registers too: 65536 / (3 x 288) = 75 per thread (72 used)
-  static constexpr int min_ctas = 3;
+  // held to in registers too: 65536 / (3 x 288) = 75 per thread (72 used),
+  // 65536 / (4 x 288) = 56 (56 used, a 4-byte spill in the gradient body)
+  static constexpr int min_ctas = wide ? 3 : 4;
 };
 
 // Sums a[0..7] over the 32 lanes; lane l returns the total of entry
