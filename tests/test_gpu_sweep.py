@@ -109,3 +109,26 @@ def test_stress_grad_sweep(G, n, k, nu, form, i):
     S, g = G.gini_stress_grad(torch.from_numpy(Y).cuda(), nu, Dd)
     assert float(S) == pytest.approx(Sref, rel=1e-5, abs=1e-12)
     assert np.max(np.abs(g.cpu().numpy() - gref)) <= 1e-5 * max(np.abs(gref).max(), 1e-30)
+
+
+@pytest.mark.parametrize("n", [2, 3, 4, 127, 128, 129, 255, 256, 257])
+@pytest.mark.parametrize("nu,form", [(1.7, "f32"), (2.0, "bf16x2"), (2.0, "fp8"), (3.3, "bf16")])
+def test_stress_grad_k3_every_tile_shape(G, n, nu, form):
+    """k = 3 with the Gini metric and Kruskal loss (the bulk-copy kernel, both
+    its general and its affine body) from one point pair to several tiles with
+    ragged edges, against the oracle on the same stored values."""
+    X = wl.gaussian_outliers(n, 5, seed=4500 + n)
+    D, sd2 = orc.delta(X, [nu])
+    D, sd2 = D[0], float(sd2[0])
+    if sd2 == 0.0:
+        pytest.skip("degenerate")
+    sc = host_col_scale(D) if form == "fp8" else None
+    Dd = G.Dissimilarity(torch.from_numpy(tile_pack(D, n, form, sc)).cuda(), n, "tiled", form,
+                         sd2, torch.from_numpy(sc).cuda() if sc is not None else None)
+    Dq = quantize(D, form, sc)
+    Dq = np.triu(Dq, 1) + np.triu(Dq, 1).T
+    Y = wl.y_init(n, 3, seed=4600 + n, sd=1.0)
+    Sref, gref = orc.stress_grad(Y.astype(np.float64), nu, Dq, sd2)
+    S, g = G.gini_stress_grad(torch.from_numpy(Y).cuda(), nu, Dd)
+    assert float(S) == pytest.approx(Sref, rel=1e-5, abs=1e-12)
+    assert np.max(np.abs(g.cpu().numpy() - gref)) <= 1e-5 * np.abs(gref).max() + 1e-12
