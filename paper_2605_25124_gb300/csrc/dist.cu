@@ -519,7 +519,11 @@ __device__ __forceinline__ void dist_keyed_body(const DistParams& P) {
         u[t] = FLT_MAX;
       }
     }
-    seg_sort_alternating<E, L, TR>(u, ls);
+    // One nu: the merge levels as a loop (the unrolled network plus the
+    // table-driven epilogue overflowed the instruction cache; 10.0 -> 9.35 ms
+    // at n = 2000, p = 784).  Several nu: unrolled (looped measured 2 % slower).
+    if constexpr (NQ == 1) seg_sort_alternating_looped<E, L, TR>(u, ls);
+    else seg_sort_alternating<E, L, TR>(u, ls);
     // every lane in ascending position order: an odd lane holds -v in reverse
     // order, so it reverses its registers and keeps the sign (equality, and so
     // the runs, do not see it; it is taken out of the lane's sums below)

@@ -167,6 +167,59 @@ __device__ __forceinline__ void seg_sort_alternating(float (&u)[E], int ls) {
   if constexpr (L >= 2) alt_level<E, L, 2>(u, ls, (ls & 1) ? -1.f : 1.f);
 }
 
+// The same sort with the merge levels as a loop: the level's lane distances
+// and each lane's role are run-time values, and the stages of all levels share
+// one copy of the code (the mirror stage, the cross-lane half-cleaners at
+// distance >= 2 and at distance 1, the in-lane half-cleaners).  Same
+// comparisons, same results; the code is several times smaller, for kernels
+// whose epilogue leaves the unrolled network short of instruction cache.
+template <int E, int L, int TR>
+__device__ __forceinline__ void seg_sort_alternating_looped(float (&u)[E], int ls) {
+  static_assert((E & (E - 1)) == 0 && (L & (L - 1)) == 0 && L <= 32 && E >= 2, "powers of two");
+  static_assert(TR >= 1 && TR <= E, "padding bound");
+  constexpr OemNet<E> net{};
+#pragma unroll
+  for (int c = 0; c < net.n; ++c)
+    if (net.b[c] < TR) cas(u[net.a[c]], u[net.b[c]]);
+  const float s0 = (ls & 1) ? -1.f : 1.f;
+#pragma unroll 1
+  for (int K = 2; K <= L; K <<= 1) {
+    float s = s0;
+    if (K >= 4) {  // the lower run (lane bit K/2 clear) keeps the minima: it carries +v
+      const float sn = (ls & (K / 2)) == 0 ? 1.f : -1.f;
+      flip(u, sn * s);
+      s = sn;
+    }
+#pragma unroll
+    for (int t = 0; t < E; ++t) {  // mirror: lane ls ^ (K-1), same register
+      const float o = __shfl_xor_sync(FULL_MASK, u[t], K - 1);
+      u[t] = fminf(u[t], -o);
+    }
+#pragma unroll 1
+    for (int D = K / 4; D >= 1; D >>= 1) {
+      const float sn = (ls & D) == 0 ? 1.f : -1.f;
+      flip(u, sn * s);
+      s = sn;
+      if (D >= 2) {
+#pragma unroll
+        for (int t = 0; t < E; ++t) {
+          const float o = __shfl_xor_sync(FULL_MASK, u[t], D);
+          u[t] = fminf(u[t], -o);
+        }
+      } else {
+#pragma unroll
+        for (int t = 0; t < E / 2; ++t) {
+          const float a = __shfl_xor_sync(FULL_MASK, u[E - 1 - t], 1);
+          const float b = __shfl_xor_sync(FULL_MASK, u[t], 1);
+          u[t] = fminf(u[t], -a);
+          u[E - 1 - t] = fminf(u[E - 1 - t], -b);
+        }
+      }
+    }
+    inlane_half_cleaners<E, E / 2>(u);  // (s is back at s0)
+  }
+}
+
 template <int E, int L, typename T>
 __device__ __forceinline__ void seg_bitonic_sort(T (&v)[E], int ls) {
   static_assert((E & (E - 1)) == 0 && (L & (L - 1)) == 0 && L <= 32 && E >= 2, "powers of two");
