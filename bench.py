@@ -168,6 +168,42 @@ def _peaks():
     return 6800.0, "fallback"
 
 
+def _network_minima(p):
+    """Minima (one ALU operation each) the Delta build's sorting network
+    issues per pair of p-vectors, over all its lanes: the layout the kernel
+    picks for p (E registers x L lanes, registers from TR up holding padding
+    that the in-lane sort skips), Batcher's odd-even sort in each lane, then
+    per merge level of K lanes one mirror stage, log2(K) - 1 cross-lane
+    half-cleaners and log2(E) in-lane half-cleaners, each E minima a lane."""
+    table = [(4, 4, 1, 4), (8, 8, 1, 8), (16, 16, 1, 16), (32, 32, 1, 32), (64, 32, 2, 32),
+             (128, 32, 4, 32), (256, 32, 8, 32), (512, 32, 16, 32), (640, 32, 32, 20),
+             (800, 32, 32, 25), (896, 32, 32, 28), (1024, 32, 32, 32)]
+    for pmax, E, L, TR in table:
+        if p <= pmax:
+            break
+    else:
+        return None  # longer vectors take the chunked kernel
+    comps, q = 0, 1
+    while q < E:  # Batcher's odd-even merge sort of E keys, comparators below TR kept
+        k = q
+        while k >= 1:
+            j = k % q
+            while j < E - k:
+                for i in range(k):
+                    a, b = i + j, i + j + k
+                    if b < E and a // (2 * q) == b // (2 * q) and b < TR:
+                        comps += 1
+                j += 2 * k
+            k //= 2
+        q *= 2
+    per_lane = 2 * comps
+    K = 2
+    while K <= L:
+        per_lane += E * (1 + (int(math.log2(K)) - 1) + int(math.log2(E)))
+        K *= 2
+    return per_lane * L
+
+
 def _profile_traffic(workload):
     """DRAM bytes per launch of the Delta-build and iteration kernels from the
     committed ncu summary, when it was captured on this workload; else {}
@@ -260,6 +296,7 @@ def run_ours(args, rank, local, world):
     # pair against the ALU pipe's rate (min/max/compare execute there: 64 lanes
     # per SM per clock on this part, half the FP32 FMA rate).
     ops_per_pair = p * math.ceil(math.log2(p))
+    net_per_pair = _network_minima(p)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     max_mhz = clocks.get("sm_max_mhz") or 2070.0
     alu_peak = sms * 64 * max_mhz * 1e6
@@ -296,6 +333,11 @@ def run_ours(args, rank, local, world):
                      "traffic": traffic.get("k_dist_bytes_per_launch"),
                      "peak_note": f"ALU pipe: {sms} SMs x 64 lanes x {max_mhz:.0f} MHz",
                      "work_note": "per pair p*ceil(log2 p) comparisons (sorting lower bound)",
+                     "network_min_per_pair": net_per_pair,
+                     "network_frac": round(P * net_per_pair / b_s / alu_peak, 4),
+                     "network_note": "minima the sorting network itself issues per pair (all "
+                                     "lanes, padding slots included) against the same peak: "
+                                     "the kernel's distance from its own ALU roof",
                      "alu_pipe_active_ncu": traffic.get("k_dist_alu_pipe_active"),
                      "alu_pipe_note": "ALU-pipe utilisation of the same kernel from an ncu capture "
                                       "(not a bench measurement): the network's own instruction "
