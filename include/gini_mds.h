@@ -47,7 +47,8 @@ typedef enum {
   GINI_OK = 0,
   GINI_EINVAL = 1,      /* invalid argument: size, null pointer, alignment, nu <= 1 */
   GINI_ENONFINITE = 2,  /* NaN or Inf in the input (reported by gini_check) */
-  GINI_EDEGENERATE = 3, /* sum of squared dissimilarities is zero: stress undefined */
+  GINI_EDEGENERATE = 3, /* sum of squared dissimilarities is zero: stress undefined
+                           (gini_fit_batched, gini_nu_search: reported by gini_check) */
   GINI_ENOMEM = 4,      /* workspace smaller than gini_workspace_size */
   GINI_ECUDA = 5,       /* a CUDA runtime call failed (see gini_last_cuda_error) */
   GINI_ETIMEOUT = 6,    /* a bounded device-side wait expired (reported by gini_check) */
@@ -150,7 +151,8 @@ int gini_get_deterministic(void);
 
 /* Synchronizes `stream`, then returns and clears the status the kernels
  * recorded in `ws` since the last gini_check (GINI_OK, GINI_ENONFINITE,
- * GINI_ETIMEOUT, or in debug builds GINI_EINDEX, which takes precedence), or
+ * GINI_EDEGENERATE, GINI_ETIMEOUT, or in debug builds GINI_EINDEX; precedence
+ * EINDEX, ETIMEOUT, EDEGENERATE, ENONFINITE), or
  * GINI_ECUDA if the stream reports an error. */
 int gini_check(void* ws, void* stream);
 
@@ -354,7 +356,9 @@ size_t gini_batch_workspace_size(const gini_problem* probs, int nprob, int n_nu,
  *   opts         gini_batch_opts, or NULL for the defaults (atomics, FP32 pool,
  *                autotuned shape); the workspace must be sized with the same
  *                options
- * Non-finite data are reported by gini_check(ws, stream). */
+ * Non-finite data are reported by gini_check(ws, stream), and so is a problem
+ * whose Delta for some nu is all zero (GINI_EDEGENERATE: its S values are then
+ * the quotient by zero). */
 int gini_fit_batched(const gini_problem* probs, int nprob, const double* nu_host, int n_nu,
                      int restarts, int iters, double eta0, const float* Y0_dev, float* Y_dev,
                      double* history_dev, double* final_stress_dev, int* tuned_config,
@@ -380,7 +384,8 @@ size_t gini_nu_search_workspace_size(int64_t n, int64_t p, const int32_t* fold_h
  *   Y_dev        n x 2 floats out: each point's embedding in its fold's best
  *                restart at nu*
  * Asynchronous on `stream` except where gini_fit_batched synchronises (its
- * first call for a batch shape times the kernel candidates). */
+ * first call for a batch shape times the kernel candidates).  A fold whose
+ * Delta is all zero is reported as GINI_EDEGENERATE by gini_check. */
 int gini_nu_search(const float* X_dev, int64_t n, int64_t p, int64_t ldx, const int32_t* fold_host,
                    int K, const double* nu_host, int n_nu, int restarts, int iters, double eta0,
                    const float* Y0_dev, double* ks_dev, double* mean_ks_dev, int* best_dev,

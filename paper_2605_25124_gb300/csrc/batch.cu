@@ -380,14 +380,19 @@ __global__ void k_batch_init(const BatchSeg* segs, int nseg, int R, const int64_
   P[sg.pt_off + (int64_t)r * sg.npad + i] = pr;
 }
 
+// A Delta whose squares sum to zero (every pseudo-distance zero) leaves the
+// normalised stress undefined: its fits are recorded as degenerate and their S
+// is left as the quotient by zero.
 __global__ void k_batch_finalize(const BatchSeg* segs, int nseg, int R, const double* sd2,
                                  const double* acc, int iters, int nfits, double* hist,
-                                 double* final_out) {
+                                 double* final_out, unsigned* err) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (int64_t)(iters + 1) * nfits) return;
   const int it = (int)(e / nfits), f = (int)(e % nfits);
   const int s = f / R;
-  const double v = acc[e] / sd2[segs[s].sd2_index];
+  const double d2 = sd2[segs[s].sd2_index];
+  if (it == 0 && !(d2 > 0.0)) raise_error(err, ERR_DEGENERATE);
+  const double v = acc[e] / d2;
   if (hist) hist[e] = v;
   if (it == iters && final_out) final_out[f] = v;
 }
@@ -752,7 +757,8 @@ extern "C" int gini_fit_batched(const gini_problem* probs, int nprob, const doub
       const int64_t nfin = (int64_t)(iters + 1) * pl.nfits;
       gini_count_launch(1);
       k_batch_finalize<<<(unsigned)((nfin + 255) / 256), 256, 0, s>>>(
-          w.segs, nseg, restarts, w.sd2, w.acc, iters, pl.nfits, history_dev, final_stress_dev);
+          w.segs, nseg, restarts, w.sd2, w.acc, iters, pl.nfits, history_dev, final_stress_dev,
+          w.err);
       s = keep;
     }
     cudaGraph_t graph;

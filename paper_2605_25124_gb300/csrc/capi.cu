@@ -92,6 +92,7 @@ extern "C" int gini_check(void* ws, void* stream) {
   if (e != cudaSuccess) { gini_set_cuda_error(e); return GINI_ECUDA; }
   if (word & ERR_INDEX) return GINI_EINDEX;  // debug builds only
   if (word & ERR_TIMEOUT) return GINI_ETIMEOUT;
+  if (word & ERR_DEGENERATE) return GINI_EDEGENERATE;
   if (word & ERR_NONFINITE) return GINI_ENONFINITE;
   return GINI_OK;
 }

@@ -20,6 +20,7 @@ constexpr int TILE = 128;  // edge B of the tiled triangle layout
 constexpr unsigned ERR_NONFINITE = 1u;
 constexpr unsigned ERR_TIMEOUT = 2u;
 constexpr unsigned ERR_INDEX = 4u;  // a debug build's index check failed
+constexpr unsigned ERR_DEGENERATE = 8u;  // a batched fit's Delta summed to zero
 
 // The first 256 bytes of every workspace hold the error word (and, in debug
 // builds, the record of the first failed index check at byte 64).

@@ -197,3 +197,35 @@ def test_batched_bf16_pool_one_step_against_the_oracle(G, tile):
                 step = Yb[a:b].reshape(n, 2) - y0
                 assert np.max(np.abs(step - (y1 - y0))) <= (1e-5 * np.abs(y1 - y0).max()
                                                            + 2e-7 * np.abs(y0).max()), (q, v, r)
+
+
+@pytest.mark.parametrize("tile", [None, (8, 2)])
+def test_batched_tiny_problems_against_the_oracle(G, tile):
+    """Problems of 2, 3, 5 and 129 points (one tile, mostly padding, and a
+    ragged second tile) with 2 to 7 features: three steps of every fit against
+    the oracle's fixed-step iterations; then a one-feature problem, whose
+    pseudo-distances are all zero (W_{1,nu} = 0), is refused as degenerate."""
+    from paper_2605_25124_gb300._lib import GiniError
+    ns, ps, nus, R, T = [2, 3, 5, 129], [2, 3, 2, 7], [1.5, 2.0], 2, 3
+    Xs, Y0s = _batch(800, ns, ps, R)
+    Xd = [torch.from_numpy(X).cuda() for X in Xs]
+    Y0 = torch.from_numpy(np.concatenate([y.reshape(-1) for y in Y0s])).cuda()
+    out = G.gini_fit_batched(Xd, nus, R, T, Y0, eta0=1.0, history=True, tile=tile)
+    hist = out["history"].cpu().numpy()
+    Yb = out["Y"].cpu().numpy()
+    sl = _slices(ns, len(nus), R)
+    for q, n in enumerate(ns):
+        D, sd2 = orc.delta(Xs[q], nus)
+        for v, nu in enumerate(nus):
+            eta = orc.default_step(n, 2, nu, sd2[v], 1.0)
+            for r in range(R):
+                y0 = Y0s[q][r * n:(r + 1) * n].astype(np.float64)
+                yT, h = orc.fit(D[v], nu, sd2[v], y0, eta, T)
+                assert np.max(np.abs(hist[:, q, v, r] - h)) <= 1e-5 * h[0] + 1e-12, (q, v, r)
+                a, b = sl[q, v, r]
+                moved = max(np.abs(yT - y0).max(), 1e-30)
+                assert np.abs(Yb[a:b].reshape(n, 2) - yT).max() <= 1e-4 * moved + 1e-6, (q, v, r)
+    X1 = [torch.from_numpy(wl.gaussian_outliers(40, 1, seed=801)).cuda()]
+    Y1 = torch.from_numpy(wl.y_init(R * 40, 2, seed=802).reshape(-1)).cuda()
+    with pytest.raises(GiniError, match="EDEGENERATE"):
+        G.gini_fit_batched(X1, nus, R, T, Y1)
