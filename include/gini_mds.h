@@ -247,7 +247,7 @@ int gini_stress_grad(const float* Y_dev, int64_t n, int k, double nu, const void
  *     (about 520,000 points at k = 2, 160,000 at k = 3) return GINI_ENOMEM
  *     before anything is enqueued.
  *   - The first call on a device looks up the array's device address with that
- *     device current; make that first call before any stream capture.
+ *     device current and keeps it for later calls.
  *   - Nothing is allocated: no cudaMalloc, no cudaFree, no allocating library
  *     routine.  The array keeps the previous call's contents; the call clears
  *     what must start at zero.
