@@ -168,16 +168,22 @@ def _peaks():
     return 6800.0, "fallback"
 
 
+# compare-exchanges of the in-lane merge of 25-register lanes (Bitonic25Net)
+BITONIC25_STEPS = 72
+
+
 def _network_minima(p):
     """Minima (one ALU operation each) the Delta build's sorting network
     issues per pair of p-vectors, over all its lanes: the layout the kernel
     picks for p (E registers x L lanes, registers from TR up holding padding
     that the in-lane sort skips), Batcher's odd-even sort in each lane, then
-    per merge level of K lanes one mirror stage, log2(K) - 1 cross-lane
-    half-cleaners and log2(E) in-lane half-cleaners, each E minima a lane."""
+    per merge level of K lanes one mirror stage and log2(K) - 1 cross-lane
+    half-cleaners, E minima a lane each, and the in-lane sort of each lane's
+    bitonic run: log2(E) half-cleaners of E minima, or for E = 25 (769 to 800
+    components) the 72 compare-exchanges of the 25-key table."""
     table = [(4, 4, 1, 4), (8, 8, 1, 8), (16, 16, 1, 16), (32, 32, 1, 32), (64, 32, 2, 32),
              (128, 32, 4, 32), (256, 32, 8, 32), (512, 32, 16, 32), (640, 32, 32, 20),
-             (800, 32, 32, 25), (896, 32, 32, 28), (1024, 32, 32, 32)]
+             (768, 32, 32, 25), (800, 25, 32, 25), (896, 32, 32, 28), (1024, 32, 32, 32)]
     for pmax, E, L, TR in table:
         if p <= pmax:
             break
@@ -197,9 +203,10 @@ def _network_minima(p):
             k //= 2
         q *= 2
     per_lane = 2 * comps
+    inlane = 2 * BITONIC25_STEPS if E == 25 else E * int(math.log2(E))
     K = 2
     while K <= L:
-        per_lane += E * (1 + (int(math.log2(K)) - 1) + int(math.log2(E)))
+        per_lane += E * int(math.log2(K)) + inlane
         K *= 2
     return per_lane * L
 

@@ -190,9 +190,12 @@ __device__ __forceinline__ void dist_body(const DistParams& P) {
   }
 
   // Affine path: sorted-position weights of the alternating layout, per
-  // (segment lane, register), zero at padding; rows padded to E + 4 floats so
-  // that the 16-byte reads of a quarter-warp fall in distinct banks.
-  __shared__ __align__(16) float s_cw[AFFINE ? L : 1][AFFINE ? E + 4 : 4];
+  // (segment lane, register), zero at padding.  A row holds CWS floats, a
+  // multiple of 4 that is 4 more or less than a multiple of 32 (E + 4 for
+  // E = 32, 28 for E = 25), so that the 16-byte reads of a quarter-warp fall
+  // in distinct banks.
+  constexpr int CWS = (E % 4 == 0) ? E + 4 : (E + 3) / 4 * 4;
+  __shared__ __align__(16) float s_cw[AFFINE ? L : 1][AFFINE ? CWS : 4];
   if constexpr (AFFINE) {
     // padding of odd lanes (negated, so at the bottom of the sorted sequence)
     int n_lo = 0;
@@ -265,11 +268,13 @@ __device__ __forceinline__ void dist_body(const DistParams& P) {
       seg_sort_alternating<E, L, TR>(u, ls);
       float2 acc2 = make_float2(0.f, 0.f);
 #pragma unroll
-      for (int t = 0; t < E; t += 4) {
+      for (int t = 0; t + 3 < E; t += 4) {
         const float4 c = *reinterpret_cast<const float4*>(&s_cw[ls][t]);
         acc2 = __ffma2_rn(make_float2(u[t], u[t + 1]), make_float2(c.x, c.y), acc2);
         acc2 = __ffma2_rn(make_float2(u[t + 2], u[t + 3]), make_float2(c.z, c.w), acc2);
       }
+#pragma unroll
+      for (int t = E / 4 * 4; t < E; ++t) acc2.x = fmaf(u[t], s_cw[ls][t], acc2.x);
       acc[0] = (acc2.x + acc2.y) * P.affine_scale;
     } else {
       // Weights that are not affine in the rank: the order must be that of the
@@ -923,6 +928,11 @@ static cudaError_t dispatch_dist(const DistParams& P, cudaStream_t s) {
     if (m <= 256) return launch_dist<32, 8, KIND, 16, 32>(P, s);
     if (m <= 512) return launch_dist<32, 16, KIND, 16, 32>(P, s);
     if (m <= 640) return launch_dist<32, 32, KIND, 16, 20>(P, s);
+    // 769..800 (28 x 28 images: 784): 25 registers per lane, none of them
+    // padding in every lane, with the 25-key in-lane merge (affine keys; the
+    // keyed kernel's tie bookkeeping assumes a power of two)
+    if constexpr (KIND == KIND_AFFINE)
+      if (m > 768 && m <= 800) return launch_dist<25, 32, KIND, 24, 25>(P, s);
     if (m <= 800) return launch_dist<32, 32, KIND, 20, 25>(P, s);
     if (m <= 896) return launch_dist<32, 32, KIND, 25, 28>(P, s);
     return launch_dist<32, 32, KIND, 28, 32>(P, s);

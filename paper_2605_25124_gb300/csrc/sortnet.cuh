@@ -75,16 +75,51 @@ __device__ __forceinline__ void inlane_half_cleaners(T (&v)[E]) {
   }
 }
 
+// A compare-exchange network that sorts every cyclic-bitonic sequence of 25
+// keys (a rotation of an ascending-then-descending run) in 72 steps; the
+// half-cleaners of a power-of-two length need 80 for 32.  It was found by a
+// randomised greedy search over 0-1 inputs: by the 0-1 principle a
+// comparator network sorts every cyclic-bitonic sequence of length 25 if and
+// only if it sorts the 602 rotations of 1^k 0^(25-k), which the CPU tests
+// re-check on this table.  Step c orders registers (a[c], b[c]), a[c] < b[c].
+struct Bitonic25Net {
+  int n = 72;
+  unsigned char a[72] = {
+      13, 14, 12, 15, 0, 1, 2, 16, 17, 3, 4, 5, 4, 3, 2, 1, 0, 5, 6, 7, 8, 9, 10, 12, 20, 21, 11,
+      10, 9, 8, 7, 6, 5, 4, 0, 1, 1, 2, 3, 0, 8, 9, 10, 11, 16, 17, 18, 19, 22, 19, 18, 15, 14, 11,
+      10, 7, 6, 3, 2, 0, 13, 1, 21, 15, 9, 3, 11, 23, 7, 19, 5, 17};
+  unsigned char b[72] = {
+      23, 22, 24, 21, 11, 10, 9, 20, 19, 8, 7, 6, 18, 17, 16, 15, 14, 19, 20, 21, 22, 23, 24, 13,
+      24, 23, 19, 18, 17, 16, 15, 14, 13, 12, 3, 2, 5, 6, 7, 4, 12, 13, 14, 15, 20, 21, 22, 23, 24,
+      21, 20, 17, 16, 13, 12, 9, 8, 5, 4, 1, 14, 2, 22, 16, 10, 4, 12, 24, 8, 20, 6, 18};
+};
+
+// Sorts the registers of a lane that hold a cyclic-bitonic sequence: the
+// half-cleaners at distances E/2, ..., 1 for a power of two E, the table
+// above for E = 25.
+template <int E, typename T>
+__device__ __forceinline__ void inlane_bitonic(T (&v)[E]) {
+  if constexpr (E == 25) {
+    constexpr Bitonic25Net net{};
+#pragma unroll
+    for (int c = 0; c < net.n; ++c) cas(v[net.a[c]], v[net.b[c]]);
+  } else {
+    static_assert((E & (E - 1)) == 0, "in-lane bitonic sort: a power of two or 25 registers");
+    inlane_half_cleaners<E, E / 2, T>(v);
+  }
+}
+
 // Multiplies every register by f (+-1) two at a time (packed f32x2, FMA pipe).
 template <int E>
 __device__ __forceinline__ void flip(float (&u)[E], float f) {
   const float2 f2 = make_float2(f, f);
 #pragma unroll
-  for (int t = 0; t < E; t += 2) {
+  for (int t = 0; t + 1 < E; t += 2) {
     const float2 p = __fmul2_rn(make_float2(u[t], u[t + 1]), f2);
     u[t] = p.x;
     u[t + 1] = p.y;
   }
+  if constexpr (E % 2) u[E - 1] *= f;
 }
 
 // Cross-lane half-cleaners of the alternating layout (below) at lane
@@ -111,6 +146,10 @@ __device__ __forceinline__ void alt_half_cleaners(float (&u)[E], int ls, float& 
         u[t] = fminf(u[t], -a);
         u[E - 1 - t] = fminf(u[E - 1 - t], -b);
       }
+      if constexpr (E % 2) {  // odd E: the middle register meets itself
+        const float o = __shfl_xor_sync(FULL_MASK, u[E / 2], 1);
+        u[E / 2] = fminf(u[E / 2], -o);
+      }
     }
     alt_half_cleaners<E, D / 2>(u, ls, s);
   }
@@ -134,7 +173,7 @@ __device__ __forceinline__ void alt_level(float (&u)[E], int ls, float s0) {
     u[t] = fminf(u[t], -o);
   }
   alt_half_cleaners<E, K / 4>(u, ls, s);  // ends with s = s0
-  inlane_half_cleaners<E, E / 2>(u);
+  inlane_bitonic(u);
   if constexpr (2 * K <= L) alt_level<E, L, 2 * K>(u, ls, s0);
 }
 
@@ -158,7 +197,8 @@ __device__ __forceinline__ void alt_level(float (&u)[E], int ls, float s0) {
 // (negated) at the bottom.
 template <int E, int L, int TR>
 __device__ __forceinline__ void seg_sort_alternating(float (&u)[E], int ls) {
-  static_assert((E & (E - 1)) == 0 && (L & (L - 1)) == 0 && L <= 32 && E >= 2, "powers of two");
+  static_assert(((E & (E - 1)) == 0 || E == 25) && (L & (L - 1)) == 0 && L <= 32 && E >= 2,
+                "E a power of two or 25, L a power of two");
   static_assert(TR >= 1 && TR <= E, "padding bound");
   constexpr OemNet<E> net{};
 #pragma unroll

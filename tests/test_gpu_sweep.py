@@ -58,7 +58,7 @@ def test_delta_sweep(G, n, p, nus, data, i):
 # nu = 2 or 3 alone: the alternating-layout network, at every boundary of its
 # dispatch (segment sizes and the padding bounds of 32-lane segments).
 P_AFFINE = [1, 2, 3, 4, 5, 8, 9, 16, 17, 32, 33, 64, 65, 128, 129, 256, 257, 512, 513, 600, 640,
-            641, 700, 784, 799, 800, 801, 896, 897, 1000, 1023, 1024]
+            641, 700, 767, 768, 769, 770, 784, 785, 792, 799, 800, 801, 896, 897, 1000, 1023, 1024]
 
 
 @pytest.mark.parametrize("p", P_AFFINE)

@@ -1,0 +1,130 @@
+"""The compile-time sorting networks of csrc/sortnet.cuh, checked on the CPU.
+
+Bitonic25Net (the in-lane merge step of 25-register lanes) is read from the
+header and checked by the 0-1 principle; then a lane-level model of the whole
+alternating-layout sort with 32 lanes x 25 registers (the Delta build of
+769..800-component vectors) is run on random keys, so that the odd register
+count of its cross-lane stages is covered as well."""
+import os
+import re
+
+import numpy as np
+
+HDR = os.path.join(os.path.dirname(__file__), "..", "paper_2605_25124_gb300", "csrc",
+                   "sortnet.cuh")
+
+
+def _table():
+    src = open(HDR).read()
+    body = re.search(r"struct Bitonic25Net \{(.*?)\n\};", src, re.S).group(1)
+    n = int(re.search(r"int n = (\d+);", body).group(1))
+    a = [int(x) for x in re.search(r"a\[\d+\] = \{(.*?)\}", body, re.S).group(1).split(",")]
+    b = [int(x) for x in re.search(r"b\[\d+\] = \{(.*?)\}", body, re.S).group(1).split(",")]
+    assert len(a) == len(b) == n
+    return list(zip(a, b))
+
+
+def _cyclic_bitonic_01(n):
+    out = set()
+    for k in range(n + 1):
+        base = [1] * k + [0] * (n - k)
+        for r in range(n):
+            out.add(tuple(base[r:] + base[:r]))
+    return sorted(out)
+
+
+def _batcher_merge_exchange(n):
+    """Batcher's odd-even merge sort for any n (Knuth, TAOCP 3, 5.2.2 M)."""
+    net, p = [], 1
+    while p < n:
+        k = p
+        while k >= 1:
+            j = k % p
+            while j < n - k:
+                for i in range(k):
+                    if i + j + k < n and (i + j) // (2 * p) == (i + j + k) // (2 * p):
+                        net.append((i + j, i + j + k))
+                j += 2 * k
+            k //= 2
+        p *= 2
+    return net
+
+
+def test_bitonic25_table_sorts_every_cyclic_bitonic_input():
+    net = _table()
+    assert all(0 <= i < j < 25 for i, j in net)
+    inputs = _cyclic_bitonic_01(25)
+    assert len(inputs) == 25 * 24 + 2
+    for v in inputs:
+        w = list(v)
+        for i, j in net:
+            if w[i] > w[j]:
+                w[i], w[j] = w[j], w[i]
+        assert w == sorted(w), v
+
+
+def _alternating_sort(u, insort, bisort):
+    """The merge levels of seg_sort_alternating on (L, E) keys, lane by lane."""
+    L, E = u.shape
+    ls = np.arange(L)
+    s0 = np.where(ls & 1, -1.0, 1.0).astype(np.float32)
+
+    def cas_all(u, net):
+        for a, b in net:
+            lo, hi = np.minimum(u[:, a], u[:, b]), np.maximum(u[:, a], u[:, b])
+            u[:, a], u[:, b] = lo, hi
+
+    cas_all(u, insort)
+    K = 2
+    while K <= L:
+        s = s0.copy()
+        if K >= 4:
+            sn = np.where(ls & (K // 2), -1.0, 1.0).astype(np.float32)
+            u *= (sn * s)[:, None]
+            s = sn
+        u = np.minimum(u, -u[ls ^ (K - 1)])
+        D = K // 4
+        while D >= 1:
+            sn = np.where(ls & D, -1.0, 1.0).astype(np.float32)
+            u *= (sn * s)[:, None]
+            s = sn
+            if D >= 2:
+                u = np.minimum(u, -u[ls ^ D])
+            else:  # opposite orientations: register t meets E-1-t
+                u = np.minimum(u, -u[ls ^ 1][:, ::-1])
+            D //= 2
+        assert np.all(s == s0)
+        cas_all(u, bisort)
+        K *= 2
+    return u
+
+
+def test_alternating_sort_with_25_registers_per_lane():
+    E, L = 25, 32
+    rng = np.random.default_rng(25)
+    insort, bisort = _batcher_merge_exchange(E), _table()
+    for m in (769, 784, 800):
+        for kind in range(3):
+            if kind == 0:
+                x = rng.standard_normal(m)
+            elif kind == 1:
+                x = rng.integers(-2, 3, m).astype(np.float64)  # many ties
+            else:
+                x = np.clip(rng.normal(0.0, 0.1, m), 0.0, 1.0)
+            x = x.astype(np.float32)
+            u = np.full((L, E), np.finfo(np.float32).max, dtype=np.float32)
+            for l in range(L):
+                for t in range(E):
+                    e = t * L + l
+                    if e < m:
+                        u[l, t] = -x[e] if l & 1 else x[e]
+            u = _alternating_sort(u, insort, bisort)
+            z = np.empty(L * E, dtype=np.float32)
+            for l in range(L):
+                for t in range(E):
+                    odd = l & 1
+                    z[E * l + (E - 1 - t if odd else t)] = -u[l, t] if odd else u[l, t]
+            # padding of odd lanes sits at the bottom, of even lanes at the top
+            n_lo = sum(E - min(E, (m - l + L - 1) // L) for l in range(1, L, 2))
+            assert np.all(np.diff(z) >= 0)
+            np.testing.assert_array_equal(z[n_lo:n_lo + m], np.sort(x))
