@@ -929,10 +929,8 @@ static cudaError_t dispatch_dist(const DistParams& P, cudaStream_t s) {
     if (m <= 512) return launch_dist<32, 16, KIND, 16, 32>(P, s);
     if (m <= 640) return launch_dist<32, 32, KIND, 16, 20>(P, s);
     // 769..800 (28 x 28 images: 784): 25 registers per lane, none of them
-    // padding in every lane, with the 25-key in-lane merge (affine keys; the
-    // keyed kernel's tie bookkeeping assumes a power of two)
-    if constexpr (KIND == KIND_AFFINE)
-      if (m > 768 && m <= 800) return launch_dist<25, 32, KIND, 24, 25>(P, s);
+    // padding in every lane, with the 25-key in-lane merge
+    if (m > 768 && m <= 800) return launch_dist<25, 32, KIND, 24, 25>(P, s);
     if (m <= 800) return launch_dist<32, 32, KIND, 20, 25>(P, s);
     if (m <= 896) return launch_dist<32, 32, KIND, 25, 28>(P, s);
     return launch_dist<32, 32, KIND, 28, 32>(P, s);

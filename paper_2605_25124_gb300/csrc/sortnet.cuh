@@ -215,7 +215,8 @@ __device__ __forceinline__ void seg_sort_alternating(float (&u)[E], int ls) {
 // whose epilogue leaves the unrolled network short of instruction cache.
 template <int E, int L, int TR>
 __device__ __forceinline__ void seg_sort_alternating_looped(float (&u)[E], int ls) {
-  static_assert((E & (E - 1)) == 0 && (L & (L - 1)) == 0 && L <= 32 && E >= 2, "powers of two");
+  static_assert(((E & (E - 1)) == 0 || E == 25) && (L & (L - 1)) == 0 && L <= 32 && E >= 2,
+                "E a power of two or 25, L a power of two");
   static_assert(TR >= 1 && TR <= E, "padding bound");
   constexpr OemNet<E> net{};
 #pragma unroll
@@ -254,9 +255,13 @@ __device__ __forceinline__ void seg_sort_alternating_looped(float (&u)[E], int l
           u[t] = fminf(u[t], -a);
           u[E - 1 - t] = fminf(u[E - 1 - t], -b);
         }
+        if constexpr (E % 2) {  // odd E: the middle register meets itself
+          const float o = __shfl_xor_sync(FULL_MASK, u[E / 2], 1);
+          u[E / 2] = fminf(u[E / 2], -o);
+        }
       }
     }
-    inlane_half_cleaners<E, E / 2>(u);  // (s is back at s0)
+    inlane_bitonic(u);  // (s is back at s0)
   }
 }
 

@@ -211,13 +211,15 @@ def test_delta_two_points_worked_example(G):
         assert mats[q].data[0, 1].item() == pytest.approx(1188 * 2.0 ** (1 - nu), rel=1e-6)
 
 
+@pytest.mark.parametrize("p", [40, 784])
 @pytest.mark.parametrize("nus", [[1.3], [1.3, 2.0, 3.7]])
-def test_delta_exact_order_of_colliding_differences(G, nus):
+def test_delta_exact_order_of_colliding_differences(G, nus, p):
     # 1 - 2^-25 rounds to 1.0f: in the pair (0, 1) it meets an exact 1.0 at the
     # top of the order, where W is steepest for nu < 2.  The two differences are
     # distinct, so their ranks must differ as in the exact (oracle) order.
+    # (p = 784: 25 registers per lane, the colliding pair in lanes 0 and 1.)
     rng = np.random.default_rng(5000)
-    n, p = 24, 40
+    n = 24
     X = rng.standard_normal((n, p)).astype(np.float32)
     X[0, :2] = [1.0, 1.0]
     X[1, :2] = [2.0 ** -25, 0.0]
@@ -260,13 +262,14 @@ def test_delta_rows_differing_by_a_constant_vector_are_zero(G, p, nus):
         G.gini_mds_fit(Y0, nus[0], D, 1.0, 3, history=False)
 
 
+@pytest.mark.parametrize("p", [47, 784])
 @pytest.mark.parametrize("nus", [[1.3], [1.3, 2.0, 3.7, 5.0]])
-def test_delta_exact_order_within_one_fp32_cell(G, nus):
+def test_delta_exact_order_within_one_fp32_cell(G, nus, p):
     # Three differences strictly between 1 and the next float up, two of them
     # equal: 1 + 2^-26 (twice) and 1 + 2^-25.  Their cell keys tie; the exact
     # order (and the tie of the equal two) must still give the oracle's ranks.
     rng = np.random.default_rng(5100)
-    n, p = 20, 47
+    n = 20
     X = rng.uniform(-0.5, 0.5, (n, p)).astype(np.float32)
     X[0, :3] = [1.0, 1.0, 1.0]
     X[1, :3] = [-2.0 ** -26, -2.0 ** -25, -2.0 ** -26]

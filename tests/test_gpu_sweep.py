@@ -76,6 +76,24 @@ def test_delta_affine_sweep(G, p, data, nu):
     assert sd2[0].item() == pytest.approx(sref[0], rel=1e-5, abs=1e-30)
 
 
+# Any other nu (the cell-key kernel) across the 25-register bucket of 769..800
+# components: one nu (merge levels as a loop), four and eight nu slots.
+@pytest.mark.parametrize("p", [767, 768, 769, 784, 800, 801])
+@pytest.mark.parametrize("nus", [[1.5], [1.3, 2.0, 3.5], [1.1, 1.4, 1.8, 2.2, 2.6, 3.0, 3.9, 4.8]])
+@pytest.mark.parametrize("data", ["gauss", "ties"])
+def test_delta_keyed_sweep_at_the_image_bucket(G, p, nus, data):
+    n = 37
+    X = _X(data, n, p, 4700 + p)
+    Dref, sref = orc.delta(X, nus)
+    mats, sd2 = G.gini_dist(torch.from_numpy(X).cuda(), nus, layout="full")
+    for v in range(len(nus)):
+        got = mats[v].data.cpu().numpy().astype(np.float64)
+        scale = max(np.abs(Dref[v]).max(), 1e-30)
+        assert np.max(np.abs(got - Dref[v])) <= 1e-5 * scale, (v, nus[v])
+        np.testing.assert_array_equal(got, got.T)
+        assert sd2[v].item() == pytest.approx(sref[v], rel=1e-5, abs=1e-30)
+
+
 def _stress_cases():
     rng = np.random.default_rng(4200)
     cases = []
