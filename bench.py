@@ -168,8 +168,16 @@ def _peaks():
     return 6800.0, "fallback"
 
 
-# compare-exchanges of the in-lane merge of 25-register lanes (Bitonic25Net)
-BITONIC25_STEPS = 72
+# compare-exchanges of the odd-length in-lane merge tables (BitonicLeaf<N>)
+BITONIC_LEAF_STEPS = {1: 0, 3: 3, 5: 8, 7: 12, 25: 72}
+
+
+def _inlane_merge_steps(E):
+    """Compare-exchanges of the in-lane merge of E registers: a half-cleaner
+    of E/2 steps and two halves while E is even, then an odd-length table."""
+    if E % 2 == 0:
+        return E // 2 + 2 * _inlane_merge_steps(E // 2)
+    return BITONIC_LEAF_STEPS[E]
 
 
 def _network_minima(p):
@@ -178,12 +186,11 @@ def _network_minima(p):
     picks for p (E registers x L lanes, registers from TR up holding padding
     that the in-lane sort skips), Batcher's odd-even sort in each lane, then
     per merge level of K lanes one mirror stage and log2(K) - 1 cross-lane
-    half-cleaners, E minima a lane each, and the in-lane sort of each lane's
-    bitonic run: log2(E) half-cleaners of E minima, or for E = 25 (769 to 800
-    components) the 72 compare-exchanges of the 25-key table."""
+    half-cleaners, E minima a lane each, and the in-lane merge of each lane's
+    bitonic run (two minima per compare-exchange)."""
     table = [(4, 4, 1, 4), (8, 8, 1, 8), (16, 16, 1, 16), (32, 32, 1, 32), (64, 32, 2, 32),
-             (128, 32, 4, 32), (256, 32, 8, 32), (512, 32, 16, 32), (640, 32, 32, 20),
-             (768, 32, 32, 25), (800, 25, 32, 25), (896, 32, 32, 28), (1024, 32, 32, 32)]
+             (128, 32, 4, 32), (256, 32, 8, 32), (512, 32, 16, 32), (640, 20, 32, 20),
+             (768, 24, 32, 24), (800, 25, 32, 25), (896, 28, 32, 28), (1024, 32, 32, 32)]
     for pmax, E, L, TR in table:
         if p <= pmax:
             break
@@ -203,7 +210,7 @@ def _network_minima(p):
             k //= 2
         q *= 2
     per_lane = 2 * comps
-    inlane = 2 * BITONIC25_STEPS if E == 25 else E * int(math.log2(E))
+    inlane = 2 * _inlane_merge_steps(E)
     K = 2
     while K <= L:
         per_lane += E * int(math.log2(K)) + inlane

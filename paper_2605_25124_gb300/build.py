@@ -46,6 +46,8 @@ def _fingerprint(flags) -> str:
     h = hashlib.sha256()
     for d in (CSRC, INCLUDE):
         for f in sorted(os.listdir(d)):
+            if not f.endswith((".cu", ".cuh", ".h")):  # sources only (not caches, scripts)
+                continue
             with open(os.path.join(d, f), "rb") as fh:
                 h.update(f.encode())
                 h.update(fh.read())

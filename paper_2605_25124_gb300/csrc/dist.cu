@@ -190,11 +190,11 @@ __device__ __forceinline__ void dist_body(const DistParams& P) {
   }
 
   // Affine path: sorted-position weights of the alternating layout, per
-  // (segment lane, register), zero at padding.  A row holds CWS floats, a
-  // multiple of 4 that is 4 more or less than a multiple of 32 (E + 4 for
-  // E = 32, 28 for E = 25), so that the 16-byte reads of a quarter-warp fall
-  // in distinct banks.
-  constexpr int CWS = (E % 4 == 0) ? E + 4 : (E + 3) / 4 * 4;
+  // (segment lane, register), zero at padding.  A row holds CWS >= E floats,
+  // an odd multiple of 4 (20 for E = 20; 28 for 24, 25, 28; 36 for 32), so
+  // that the rows of 8 consecutive lanes start in 8 distinct groups of 4 banks
+  // and the 16-byte reads of a quarter-warp do not conflict.
+  constexpr int CWS = ((E + 3) / 4) % 2 ? (E + 3) / 4 * 4 : (E + 3) / 4 * 4 + 4;
   __shared__ __align__(16) float s_cw[AFFINE ? L : 1][AFFINE ? CWS : 4];
   if constexpr (AFFINE) {
     // padding of odd lanes (negated, so at the bottom of the sorted sequence)
@@ -900,11 +900,11 @@ static cudaError_t launch_dist(const DistParams& P, cudaStream_t s) {
 }
 
 // Segment shapes by vector length m: one instantiation per power-of-two
-// segment size, with the bounds TL, TR on the real registers (m in
-// (E*L/2, E*L] fills every register below E/2), the 32-lane segments split
-// further by m so that the in-lane sort skips the comparators of registers
-// that only ever hold padding (m = 784: 25 of 32).  The 64-bit network takes
-// the plain power-of-two shapes.
+// segment size up to 16 lanes, with the bounds TL, TR on the real registers
+// (m in (E*L/2, E*L] fills every register below E/2); 32-lane segments take
+// 20, 24, 25, 28 or 32 registers per lane by m, so that no register holds
+// padding in every lane.  The 64-bit network takes the plain power-of-two
+// shapes.
 template <int KIND>
 static cudaError_t dispatch_dist(const DistParams& P, cudaStream_t s) {
   const int64_t m = P.m;
@@ -927,12 +927,13 @@ static cudaError_t dispatch_dist(const DistParams& P, cudaStream_t s) {
     if (m <= 128) return launch_dist<32, 4, KIND, 16, 32>(P, s);
     if (m <= 256) return launch_dist<32, 8, KIND, 16, 32>(P, s);
     if (m <= 512) return launch_dist<32, 16, KIND, 16, 32>(P, s);
-    if (m <= 640) return launch_dist<32, 32, KIND, 16, 20>(P, s);
-    // 769..800 (28 x 28 images: 784): 25 registers per lane, none of them
-    // padding in every lane, with the 25-key in-lane merge
-    if (m > 768 && m <= 800) return launch_dist<25, 32, KIND, 24, 25>(P, s);
-    if (m <= 800) return launch_dist<32, 32, KIND, 20, 25>(P, s);
-    if (m <= 896) return launch_dist<32, 32, KIND, 25, 28>(P, s);
+    // 32 lanes: each holds as many registers as the data need, rounded to a
+    // length with a short in-lane merge (20, 24, 25, 28, 32), so that no
+    // register is padding in every lane (784 = 28 x 28 images: 25)
+    if (m <= 640) return launch_dist<20, 32, KIND, 16, 20>(P, s);
+    if (m <= 768) return launch_dist<24, 32, KIND, 20, 24>(P, s);
+    if (m <= 800) return launch_dist<25, 32, KIND, 24, 25>(P, s);
+    if (m <= 896) return launch_dist<28, 32, KIND, 25, 28>(P, s);
     return launch_dist<32, 32, KIND, 28, 32>(P, s);
   }
 }

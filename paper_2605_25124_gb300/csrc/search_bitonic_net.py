@@ -1,14 +1,17 @@
-"""Searches for the in-lane network of sortnet.cuh's Bitonic25Net.
+"""Searches for the odd-length in-lane merge tables of sortnet.cuh (BitonicLeaf).
 
 By the 0-1 principle a comparator network sorts every cyclic-bitonic
 sequence of n keys (a rotation of an ascending-then-descending run) if and
 only if it sorts every rotation of 1^k 0^(n-k), k = 0..n.  The search is
 greedy: from the set of those 0-1 inputs it repeatedly appends the
 compare-exchange (i < j) that leaves the fewest distinct outputs (ties broken
-by a seeded shuffle) until every output is sorted.  Seed 14 gives the
-72-step table in sortnet.cuh:
+by a seeded shuffle) until every output is sorted.  The tables in
+sortnet.cuh come from
 
-    python search_bitonic25.py --seed 14
+    python search_bitonic_net.py --n 3 --seed 0     # 3 steps
+    python search_bitonic_net.py --n 5 --seed 0     # 8 steps
+    python search_bitonic_net.py --n 7 --seed 0     # 12 steps
+    python search_bitonic_net.py --n 25 --seed 14   # 72 steps (shortest of 5,600 seeds)
 """
 import argparse
 import random

@@ -17,7 +17,11 @@
 // Float keys (seg_sort_alternating): the same merges on a layout in which
 // odd lanes hold negated values in reverse order, so that every exchange is
 // one minimum; the in-lane sort is Batcher's odd-even merge sort (191
-// compare-exchanges instead of 240 bitonic ones for E = 32).
+// compare-exchanges instead of 240 bitonic ones for E = 32).  E need not be a
+// power of two: the lanes then hold exactly as many registers as the data
+// need (25 for 784 keys over 32 lanes), the cross-lane stages are
+// half-cleaners on blocks of 2 D E positions, exact for any even length, and
+// the in-lane merge recurses down to odd-length tables (inlane_bitonic).
 #pragma once
 
 #include "common.cuh"
@@ -75,14 +79,47 @@ __device__ __forceinline__ void inlane_half_cleaners(T (&v)[E]) {
   }
 }
 
-// A compare-exchange network that sorts every cyclic-bitonic sequence of 25
-// keys (a rotation of an ascending-then-descending run) in 72 steps; the
-// half-cleaners of a power-of-two length need 80 for 32.  It was found by a
-// randomised greedy search over 0-1 inputs: by the 0-1 principle a
-// comparator network sorts every cyclic-bitonic sequence of length 25 if and
-// only if it sorts the 602 rotations of 1^k 0^(25-k), which the CPU tests
-// re-check on this table.  Step c orders registers (a[c], b[c]), a[c] < b[c].
-struct Bitonic25Net {
+// In-lane merge of a lane's registers once they hold a cyclic-bitonic
+// sequence (a rotation of an ascending-then-descending run).  A half-cleaner
+// (t against t + N/2) splits a cyclic-bitonic sequence of any even length N
+// into two cyclic-bitonic halves, every key of the first no greater than any
+// key of the second; so even lengths recurse on their halves, and the odd
+// lengths at the end of the recursion take a table (BitonicLeaf).  Powers of
+// two give the usual half-cleaners (80 steps for 32 registers); 20 registers
+// take 52, 24 take 60, 25 take 72, 28 take 76.
+//
+// The tables sort every cyclic-bitonic sequence of their length.  They were
+// found by a seeded greedy search over 0-1 inputs (search_bitonic_net.py): by
+// the 0-1 principle a comparator network sorts every cyclic-bitonic sequence of
+// length N if and only if it sorts the rotations of 1^k 0^(N-k), which the CPU
+// tests re-check on these tables.  Step c orders registers (a[c], b[c]),
+// a[c] < b[c].
+template <int N>
+struct BitonicLeaf;  // defined for the odd lengths that occur
+
+template <>
+struct BitonicLeaf<3> {
+  int n = 3;
+  unsigned char a[3] = {0, 0, 1};
+  unsigned char b[3] = {1, 2, 2};
+};
+
+template <>
+struct BitonicLeaf<5> {
+  int n = 8;
+  unsigned char a[8] = {2, 0, 0, 1, 1, 0, 2, 3};
+  unsigned char b[8] = {4, 3, 2, 4, 2, 1, 3, 4};
+};
+
+template <>
+struct BitonicLeaf<7> {
+  int n = 12;
+  unsigned char a[12] = {1, 2, 3, 1, 0, 5, 0, 3, 4, 4, 2, 0};
+  unsigned char b[12] = {6, 5, 4, 3, 4, 6, 2, 5, 6, 5, 3, 1};
+};
+
+template <>
+struct BitonicLeaf<25> {
   int n = 72;
   unsigned char a[72] = {
       13, 14, 12, 15, 0, 1, 2, 16, 17, 3, 4, 5, 4, 3, 2, 1, 0, 5, 6, 7, 8, 9, 10, 12, 20, 21, 11,
@@ -94,19 +131,24 @@ struct Bitonic25Net {
       21, 20, 17, 16, 13, 12, 9, 8, 5, 4, 1, 14, 2, 22, 16, 10, 4, 12, 24, 8, 20, 6, 18};
 };
 
-// Sorts the registers of a lane that hold a cyclic-bitonic sequence: the
-// half-cleaners at distances E/2, ..., 1 for a power of two E, the table
-// above for E = 25.
+// Sorts registers v[OFF .. OFF+N) holding a cyclic-bitonic sequence.
+template <int OFF, int N, int E, typename T>
+__device__ __forceinline__ void bitonic_window(T (&v)[E]) {
+  if constexpr (N % 2 == 0 && N >= 2) {
+#pragma unroll
+    for (int t = 0; t < N / 2; ++t) cas(v[OFF + t], v[OFF + t + N / 2]);
+    bitonic_window<OFF, N / 2, E, T>(v);
+    bitonic_window<OFF + N / 2, N / 2, E, T>(v);
+  } else if constexpr (N > 1) {
+    constexpr BitonicLeaf<N> net{};
+#pragma unroll
+    for (int c = 0; c < net.n; ++c) cas(v[OFF + net.a[c]], v[OFF + net.b[c]]);
+  }
+}
+
 template <int E, typename T>
 __device__ __forceinline__ void inlane_bitonic(T (&v)[E]) {
-  if constexpr (E == 25) {
-    constexpr Bitonic25Net net{};
-#pragma unroll
-    for (int c = 0; c < net.n; ++c) cas(v[net.a[c]], v[net.b[c]]);
-  } else {
-    static_assert((E & (E - 1)) == 0, "in-lane bitonic sort: a power of two or 25 registers");
-    inlane_half_cleaners<E, E / 2, T>(v);
-  }
+  bitonic_window<0, E, E, T>(v);
 }
 
 // Multiplies every register by f (+-1) two at a time (packed f32x2, FMA pipe).
@@ -197,8 +239,7 @@ __device__ __forceinline__ void alt_level(float (&u)[E], int ls, float s0) {
 // (negated) at the bottom.
 template <int E, int L, int TR>
 __device__ __forceinline__ void seg_sort_alternating(float (&u)[E], int ls) {
-  static_assert(((E & (E - 1)) == 0 || E == 25) && (L & (L - 1)) == 0 && L <= 32 && E >= 2,
-                "E a power of two or 25, L a power of two");
+  static_assert((L & (L - 1)) == 0 && L <= 32 && E >= 2, "L a power of two");
   static_assert(TR >= 1 && TR <= E, "padding bound");
   constexpr OemNet<E> net{};
 #pragma unroll
@@ -215,8 +256,7 @@ __device__ __forceinline__ void seg_sort_alternating(float (&u)[E], int ls) {
 // whose epilogue leaves the unrolled network short of instruction cache.
 template <int E, int L, int TR>
 __device__ __forceinline__ void seg_sort_alternating_looped(float (&u)[E], int ls) {
-  static_assert(((E & (E - 1)) == 0 || E == 25) && (L & (L - 1)) == 0 && L <= 32 && E >= 2,
-                "E a power of two or 25, L a power of two");
+  static_assert((L & (L - 1)) == 0 && L <= 32 && E >= 2, "L a power of two");
   static_assert(TR >= 1 && TR <= E, "padding bound");
   constexpr OemNet<E> net{};
 #pragma unroll

@@ -56,7 +56,7 @@ def test_delta_sweep(G, n, p, nus, data, i):
 
 
 # nu = 2 or 3 alone: the alternating-layout network, at every boundary of its
-# dispatch (segment sizes and the padding bounds of 32-lane segments).
+# dispatch (segment sizes, and the register counts of 32-lane segments).
 P_AFFINE = [1, 2, 3, 4, 5, 8, 9, 16, 17, 32, 33, 64, 65, 128, 129, 256, 257, 512, 513, 600, 640,
             641, 700, 767, 768, 769, 770, 784, 785, 792, 799, 800, 801, 896, 897, 1000, 1023, 1024]
 
@@ -76,12 +76,13 @@ def test_delta_affine_sweep(G, p, data, nu):
     assert sd2[0].item() == pytest.approx(sref[0], rel=1e-5, abs=1e-30)
 
 
-# Any other nu (the cell-key kernel) across the 25-register bucket of 769..800
-# components: one nu (merge levels as a loop), four and eight nu slots.
-@pytest.mark.parametrize("p", [767, 768, 769, 784, 800, 801])
+# Any other nu (the cell-key kernel) at the edges of the 32-lane shapes (20,
+# 24, 25, 28 and 32 registers per lane): one nu (merge levels as a loop), four
+# and eight nu slots.
+@pytest.mark.parametrize("p", [512, 513, 640, 641, 767, 768, 769, 784, 800, 801, 896, 897])
 @pytest.mark.parametrize("nus", [[1.5], [1.3, 2.0, 3.5], [1.1, 1.4, 1.8, 2.2, 2.6, 3.0, 3.9, 4.8]])
 @pytest.mark.parametrize("data", ["gauss", "ties"])
-def test_delta_keyed_sweep_at_the_image_bucket(G, p, nus, data):
+def test_delta_keyed_sweep_at_the_32_lane_shapes(G, p, nus, data):
     n = 37
     X = _X(data, n, p, 4700 + p)
     Dref, sref = orc.delta(X, nus)

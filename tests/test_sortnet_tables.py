@@ -1,27 +1,42 @@
 """The compile-time sorting networks of csrc/sortnet.cuh, checked on the CPU.
 
-Bitonic25Net (the in-lane merge step of 25-register lanes) is read from the
-header and checked by the 0-1 principle; then a lane-level model of the whole
-alternating-layout sort with 32 lanes x 25 registers (the Delta build of
-769..800-component vectors) is run on random keys, so that the odd register
-count of its cross-lane stages is covered as well."""
+The odd-length in-lane merge tables (BitonicLeaf<N>) are read from the header
+and checked by the 0-1 principle; then a lane-level model of the whole
+alternating-layout sort with 32 lanes x E registers (E = 20, 24, 25, 28, 32:
+the Delta build's 32-lane shapes) is run on random keys, so that the
+non-power-of-two register counts of its cross-lane stages and the recursive
+in-lane merge are covered as well."""
 import os
 import re
 
 import numpy as np
+import pytest
 
 HDR = os.path.join(os.path.dirname(__file__), "..", "paper_2605_25124_gb300", "csrc",
                    "sortnet.cuh")
 
 
-def _table():
+def _leaves():
     src = open(HDR).read()
-    body = re.search(r"struct Bitonic25Net \{(.*?)\n\};", src, re.S).group(1)
-    n = int(re.search(r"int n = (\d+);", body).group(1))
-    a = [int(x) for x in re.search(r"a\[\d+\] = \{(.*?)\}", body, re.S).group(1).split(",")]
-    b = [int(x) for x in re.search(r"b\[\d+\] = \{(.*?)\}", body, re.S).group(1).split(",")]
-    assert len(a) == len(b) == n
-    return list(zip(a, b))
+    out = {}
+    for N, body in re.findall(r"struct BitonicLeaf<(\d+)> \{(.*?)\n\};", src, re.S):
+        n = int(re.search(r"int n = (\d+);", body).group(1))
+        a = [int(x) for x in re.search(r"a\[\d+\] = \{(.*?)\}", body, re.S).group(1).split(",")]
+        b = [int(x) for x in re.search(r"b\[\d+\] = \{(.*?)\}", body, re.S).group(1).split(",")]
+        assert len(a) == len(b) == n
+        out[int(N)] = list(zip(a, b))
+    return out
+
+
+def _inlane_bitonic(E, leaves, off=0):
+    """Compare-exchanges of bitonic_window<off, E>: half-cleaners down to odd leaves."""
+    if E % 2 == 0 and E >= 2:
+        h = E // 2
+        return ([(off + t, off + t + h) for t in range(h)] + _inlane_bitonic(h, leaves, off) +
+                _inlane_bitonic(h, leaves, off + h))
+    if E > 1:
+        return [(off + i, off + j) for i, j in leaves[E]]
+    return []
 
 
 def _cyclic_bitonic_01(n):
@@ -50,12 +65,26 @@ def _batcher_merge_exchange(n):
     return net
 
 
-def test_bitonic25_table_sorts_every_cyclic_bitonic_input():
-    net = _table()
-    assert all(0 <= i < j < 25 for i, j in net)
-    inputs = _cyclic_bitonic_01(25)
-    assert len(inputs) == 25 * 24 + 2
-    for v in inputs:
+def test_leaf_tables_sort_every_cyclic_bitonic_input():
+    leaves = _leaves()
+    assert sorted(leaves) == [3, 5, 7, 25]
+    assert {N: len(net) for N, net in leaves.items()} == {3: 3, 5: 8, 7: 12, 25: 72}
+    for N, net in leaves.items():
+        assert all(0 <= i < j < N for i, j in net)
+        inputs = _cyclic_bitonic_01(N)
+        assert len(inputs) == N * (N - 1) + 2
+        for v in inputs:
+            w = list(v)
+            for i, j in net:
+                if w[i] > w[j]:
+                    w[i], w[j] = w[j], w[i]
+            assert w == sorted(w), (N, v)
+
+
+@pytest.mark.parametrize("E", [20, 24, 25, 28, 32])
+def test_inlane_merge_sorts_every_cyclic_bitonic_input(E):
+    net = _inlane_bitonic(E, _leaves())
+    for v in _cyclic_bitonic_01(E):
         w = list(v)
         for i, j in net:
             if w[i] > w[j]:
@@ -99,11 +128,14 @@ def _alternating_sort(u, insort, bisort):
     return u
 
 
-def test_alternating_sort_with_25_registers_per_lane():
-    E, L = 25, 32
-    rng = np.random.default_rng(25)
-    insort, bisort = _batcher_merge_exchange(E), _table()
-    for m in (769, 784, 800):
+@pytest.mark.parametrize("E,ms", [(20, (513, 600, 640)), (24, (641, 700, 768)),
+                                  (25, (769, 784, 800)), (28, (801, 850, 896)),
+                                  (32, (897, 1000, 1024))])
+def test_alternating_sort_32_lanes(E, ms):
+    L = 32
+    rng = np.random.default_rng(E)
+    insort, bisort = _batcher_merge_exchange(E), _inlane_bitonic(E, _leaves())
+    for m in ms:
         for kind in range(3):
             if kind == 0:
                 x = rng.standard_normal(m)
