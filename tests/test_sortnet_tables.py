@@ -160,3 +160,17 @@ def test_alternating_sort_32_lanes(E, ms):
             n_lo = sum(E - min(E, (m - l + L - 1) // L) for l in range(1, L, 2))
             assert np.all(np.diff(z) >= 0)
             np.testing.assert_array_equal(z[n_lo:n_lo + m], np.sort(x))
+
+
+def test_bench_counts_the_network_the_header_defines():
+    # bench.py's network_frac counts the minima of the tables above
+    import sys
+    sys.path.insert(0, os.path.join(os.path.dirname(__file__), ".."))
+    import bench
+    leaves = _leaves()
+    assert {N: len(net) for N, net in leaves.items()} == \
+        {N: c for N, c in bench.BITONIC_LEAF_STEPS.items() if N > 1}
+    for E in (20, 24, 25, 28, 32):
+        assert bench._inlane_merge_steps(E) == len(_inlane_bitonic(E, leaves))
+    # p = 784: 32 lanes x (2 x 140 odd-even + 15 x 25 cross-lane + 5 x 2 x 72 in-lane)
+    assert bench._network_minima(784) == 32 * (280 + 375 + 720)
