@@ -80,8 +80,10 @@ def selftest_index_check():
 
 
 def delta_full_every_family():
+    # 784: 25 registers per lane; 600, 700, 850: 20, 24, 28 (the other 32-lane shapes)
     for n, p, nus in ((41, 784, [2.0]), (41, 784, [1.5, 2.5]), (33, 50, [1.5, 2.0, 3.0]),
-                      (29, 7, [3.0])):
+                      (29, 7, [3.0]), (23, 600, [2.0]), (23, 700, [1.5]),
+                      (23, 850, [2.0, 3.5])):
         X = wl.gaussian_outliers(n, p, seed=900 + p + len(nus))
         ref, sref = orc.delta(X, nus)
         mats, sd2 = G.gini_dist(torch.from_numpy(X).cuda(), nus, layout="full")
