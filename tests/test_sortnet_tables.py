@@ -2,10 +2,10 @@
 
 The odd-length in-lane merge tables (BitonicLeaf<N>) are read from the header
 and checked by the 0-1 principle; then a lane-level model of the whole
-alternating-layout sort with 32 lanes x E registers (E = 20, 24, 25, 28, 32:
-the Delta build's 32-lane shapes) is run on random keys, so that the
-non-power-of-two register counts of its cross-lane stages and the recursive
-in-lane merge are covered as well."""
+alternating-layout sort is run on random keys for every shape the Delta build
+dispatches: 32 lanes x E registers (E = 20, 24, 25, 28, 32), so that the
+non-power-of-two register counts of the cross-lane stages and the recursive
+in-lane merge are covered, and the segments of 1 to 16 lanes."""
 import os
 import re
 
@@ -174,3 +174,30 @@ def test_bench_counts_the_network_the_header_defines():
         assert bench._inlane_merge_steps(E) == len(_inlane_bitonic(E, leaves))
     # p = 784: 32 lanes x (2 x 140 odd-even + 15 x 25 cross-lane + 5 x 2 x 72 in-lane)
     assert bench._network_minima(784) == 32 * (280 + 375 + 720)
+
+
+@pytest.mark.parametrize("E,L,ms", [(4, 1, (1, 3, 4)), (8, 1, (5, 8)), (16, 1, (9, 16)),
+                                    (32, 1, (17, 32)), (32, 2, (33, 50, 64)),
+                                    (32, 4, (65, 100, 128)), (32, 8, (129, 200, 256)),
+                                    (32, 16, (257, 300, 512))])
+def test_alternating_sort_narrow_segments(E, L, ms):
+    # segments of 1 to 16 lanes (the shapes below 513 components): one segment
+    rng = np.random.default_rng(100 * L + E)
+    insort, bisort = _batcher_merge_exchange(E), _inlane_bitonic(E, _leaves())
+    for m in ms:
+        x = rng.integers(-3, 4, m).astype(np.float32) * np.float32(0.5)
+        u = np.full((L, E), np.finfo(np.float32).max, dtype=np.float32)
+        for l in range(L):
+            for t in range(E):
+                e = t * L + l
+                if e < m:
+                    u[l, t] = -x[e] if (L >= 2 and l & 1) else x[e]
+        u = _alternating_sort(u, insort, bisort)
+        z = np.empty(L * E, dtype=np.float32)
+        for l in range(L):
+            for t in range(E):
+                odd = L >= 2 and (l & 1)
+                z[E * l + (E - 1 - t if odd else t)] = -u[l, t] if odd else u[l, t]
+        n_lo = sum(E - min(E, (m - l + L - 1) // L) for l in range(1, L, 2)) if L >= 2 else 0
+        assert np.all(np.diff(z) >= 0)
+        np.testing.assert_array_equal(z[n_lo:n_lo + m], np.sort(x))
