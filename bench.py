@@ -63,7 +63,44 @@ def _args():
                     help="skip the nu-grid build and the batched configuration")
     ap.add_argument("--form", default="f32", choices=list(FORMS),
                     help="storage of Delta in the timed fits")
+    ap.add_argument("--dist-shapes", action="store_true",
+                    help="instead of the fit: time gini_dist at n = 6,000 for vector lengths "
+                         "across the 32-lane shapes (20 to 32 registers per lane)")
     return ap.parse_args()
+
+
+def run_dist_shapes(dev):
+    """gini_dist (tiled FP32) at n = 6,000, uniform data, for p in each 32-lane
+    register count's range, nu = 2 (affine kernel) and nu = 1.5 (cell keys):
+    median of five calls after one warm-up, CUDA events on the launching
+    stream.  Reports ms and the network's minima per pair for each p."""
+    import torch
+    import paper_2605_25124_gb300 as G
+    from paper_2605_25124_gb300 import build as gb
+    gb.build()
+    n = 6000
+    stream = torch.cuda.current_stream(dev)
+    res = {}
+    for p in (520, 600, 640, 700, 768, 784, 850, 896, 1000):
+        g = torch.Generator().manual_seed(p)
+        X = torch.rand(n, p, generator=g).to(dev)
+        row = {"network_min_per_pair": _network_minima(p)}
+        for nus in ([2.0], [1.5]):
+            G.gini_dist(X, nus, layout="tiled", dtype="f32")
+            ts = []
+            for _ in range(5):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record(stream)
+                G.gini_dist(X, nus, layout="tiled", dtype="f32")
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            row[f"nu_{nus[0]}_ms"] = round(statistics.median(ts), 3)
+        res[str(p)] = row
+    return {"dist_shapes": {"n": n, "data": "uniform [0, 1)", "layout": "tiled f32",
+                            "by_p": res}}
 
 
 def _dist_init(args):
@@ -742,6 +779,10 @@ def main():
     rank, local, world = _dist_init(args)
     if args.impl == "reference":
         out = run_reference(args, rank, world)
+    elif args.dist_shapes:
+        import torch
+        torch.cuda.set_device(local)
+        out = run_dist_shapes(torch.device("cuda", local)) if rank == 0 else None
     elif args.workload.startswith("uci-batch"):
         out = run_batched(args, rank, local, world)
     else:
